@@ -1,0 +1,474 @@
+/*
+ * gns_oracle.c -- CPU oracle for the stable mergesort hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check of the build entry
+ * point and the CPU-baseline leg of the benchmark may load this library.  The
+ * product path (the CUDA library under paper_2402_01816_gb300/) never calls,
+ * links or includes anything from here, and this file includes nothing from
+ * there: the two implementations share no code.
+ *
+ * Everything is plain, sequential, obviously-checkable C:
+ *
+ *   orc_compare          the total order on 64-bit keys ("Definition of sorting"
+ *                        chapter; -0.0/NaN handled by the IEEE 754 totalOrder
+ *                        reading).
+ *   orc_stable_sort      THE definition of the result: sort (key, input index)
+ *                        pairs lexicographically with the C library qsort and
+ *                        gather.  Stable sorting has exactly one correct result
+ *                        ("Definition of sorting": AscLeft / DescLeft targets).
+ *   orc_knuthsort        the paper's prior-art reference mergesort: Nocopy
+ *                        alternation between two 100% regions plus Knuth's merge
+ *                        with a single exhaustion check ("Forgotten art" section).
+ *   orc_frogsort         symmetric merging with at most 50% local buffer:
+ *                        Frogsort1 (single-element splits, surplus element to the
+ *                        outer side, buffer = N/2 integer division; "Frogsort1"
+ *                        section) and Frogsort0 (triplet splits; "Frogsort0"
+ *                        section), recursive setup then recursive split & merge,
+ *                        merging from the inner to the outer input streams
+ *                        ("Symmetric merging" section).
+ *   orc_frog_trace       position-label trace of the Frogsort layout after each
+ *                        recursion depth, to be compared with the two layout
+ *                        tables printed in the Frogsort0 and Frogsort1 sections.
+ *   orc_segmented_sort   the definition applied to each segment independently.
+ *   orc_final_position   where one input element ends up (rank counting), for
+ *                        sampled checks of outputs too large to sort here.
+ *
+ * Keys are passed as raw 64-bit patterns (float64 or int64); payloads are uint32.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { ORC_F64 = 0, ORC_I64 = 1 };
+enum { ORC_ASC = 0, ORC_DESC = 1 };
+
+/* ------------------------------------------------------------------------ */
+/* Total order                                                                */
+/* ------------------------------------------------------------------------ */
+
+/* Ascending total order of two raw key patterns: -1, 0, +1.
+ *
+ * int64: two's complement signed comparison.
+ * float64: IEEE 754 totalOrder.  A key with the sign bit set is below every key
+ * without it.  Among non-negative patterns (+0, positive numbers, +inf, +NaN)
+ * the unsigned bit patterns order like the magnitudes.  Among negative patterns
+ * the order of the magnitudes is reversed.  So -NaN < -inf < ... < -0.0 < +0.0
+ * < ... < +inf < +NaN, with NaNs ordered by their payload bits.  The paper does
+ * not discuss -0.0 or NaN; this is the reading the library documents. */
+int orc_compare(uint64_t a, uint64_t b, int key_type)
+{
+    if (key_type == ORC_I64) {
+        int64_t x = (int64_t)a, y = (int64_t)b;
+        return (x < y) ? -1 : (x > y) ? 1 : 0;
+    }
+    int sa = (int)(a >> 63), sb = (int)(b >> 63);
+    if (sa != sb) return sa ? -1 : 1;          /* negative below positive */
+    uint64_t ma = a & 0x7fffffffffffffffull, mb = b & 0x7fffffffffffffffull;
+    if (ma == mb) return 0;
+    if (!sa) return (ma < mb) ? -1 : 1;        /* both non-negative */
+    return (ma < mb) ? 1 : -1;                 /* both negative: reversed */
+}
+
+/* Order used for a sort call: ascending, or descending (keys non-increasing
+ * from left to right).  Ties are never decided here: callers keep input order
+ * among equal keys (AscLeft / DescLeft). */
+static int ord_cmp(uint64_t a, uint64_t b, int key_type, int order)
+{
+    int c = orc_compare(a, b, key_type);
+    return order == ORC_DESC ? -c : c;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The definition: sort (key, index) pairs                                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { uint64_t key; int64_t idx; } orc_rec;
+static int g_key_type, g_order;   /* qsort has no context argument */
+
+static int rec_cmp(const void* pa, const void* pb)
+{
+    const orc_rec* a = (const orc_rec*)pa;
+    const orc_rec* b = (const orc_rec*)pb;
+    int c = ord_cmp(a->key, b->key, g_key_type, g_order);
+    if (c) return c;
+    return (a->idx < b->idx) ? -1 : (a->idx > b->idx) ? 1 : 0;
+}
+
+/* Returns 0 on success, -1 on allocation failure. payload may be NULL. */
+int orc_stable_sort(uint64_t* keys, uint32_t* payload, int64_t n, int key_type, int order)
+{
+    if (n <= 1) return 0;
+    orc_rec* r = (orc_rec*)malloc((size_t)n * sizeof(orc_rec));
+    uint32_t* p = payload ? (uint32_t*)malloc((size_t)n * sizeof(uint32_t)) : NULL;
+    if (!r || (payload && !p)) { free(r); free(p); return -1; }
+    for (int64_t i = 0; i < n; i++) { r[i].key = keys[i]; r[i].idx = i; }
+    if (payload) memcpy(p, payload, (size_t)n * sizeof(uint32_t));
+    g_key_type = key_type; g_order = order;
+    qsort(r, (size_t)n, sizeof(orc_rec), rec_cmp);
+    for (int64_t i = 0; i < n; i++) {
+        keys[i] = r[i].key;
+        if (payload) payload[i] = p[r[i].idx];
+    }
+    free(r); free(p);
+    return 0;
+}
+
+/* Final position of input element i in the stable sort: the number of keys
+ * strictly before it in the order, plus the number of equal keys earlier in
+ * the input. */
+int64_t orc_final_position(const uint64_t* keys, int64_t n, int key_type, int order, int64_t i)
+{
+    int64_t pos = 0;
+    for (int64_t k = 0; k < n; k++) {
+        int c = ord_cmp(keys[k], keys[i], key_type, order);
+        if (c < 0 || (c == 0 && k < i)) pos++;
+    }
+    return pos;
+}
+
+/* Same as orc_stable_sort, independently per segment [off[s], off[s+1]). */
+int orc_segmented_sort(uint64_t* keys, uint32_t* payload, const int64_t* offsets,
+                       int64_t nseg, int key_type, int order)
+{
+    for (int64_t s = 0; s < nseg; s++) {
+        int64_t a = offsets[s], len = offsets[s + 1] - offsets[s];
+        if (orc_stable_sort(keys + a, payload ? payload + a : NULL, len, key_type, order))
+            return -1;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Knuthsort: Nocopy mergesort with Knuth's merge                            */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int key_type, order;
+    int64_t moves, compares;
+} orc_ctx;
+
+/* Merge the sorted runs src[lo..mid) and src[mid..hi) into dst[lo..hi).  Knuth's
+ * merge checks for exhaustion only the run whose element was just taken.  Ties
+ * take the left run (stability). */
+static void knuth_merge(orc_ctx* c, const uint64_t* sk, const uint32_t* sp,
+                        uint64_t* dk, uint32_t* dp, int64_t lo, int64_t mid, int64_t hi)
+{
+    int64_t i = lo, j = mid, k = lo;
+    for (;;) {
+        c->compares++;
+        if (ord_cmp(sk[j], sk[i], c->key_type, c->order) < 0) {
+            dk[k] = sk[j]; if (dp) dp[k] = sp[j]; k++; j++; c->moves++;
+            if (j == hi) {            /* right run exhausted: copy rest of left */
+                while (i < mid) { dk[k] = sk[i]; if (dp) dp[k] = sp[i]; k++; i++; c->moves++; }
+                return;
+            }
+        } else {
+            dk[k] = sk[i]; if (dp) dp[k] = sp[i]; k++; i++; c->moves++;
+            if (i == mid) {           /* left run exhausted: copy rest of right */
+                while (j < hi) { dk[k] = sk[j]; if (dp) dp[k] = sp[j]; k++; j++; c->moves++; }
+                return;
+            }
+        }
+    }
+}
+
+/* Sort [lo, hi) so that the result lies in (ak, ap), using (bk, bp) which holds
+ * an identical copy of the data on entry.  The two halves are sorted into the
+ * other region and merged back: the regions alternate per recursion level and
+ * no element is ever copied without being merged (Nocopy). */
+static void knuth_rec(orc_ctx* c, uint64_t* ak, uint32_t* ap, uint64_t* bk, uint32_t* bp,
+                      int64_t lo, int64_t hi)
+{
+    if (hi - lo < 2) return;
+    int64_t mid = lo + (hi - lo) / 2;
+    knuth_rec(c, bk, bp, ak, ap, lo, mid);
+    knuth_rec(c, bk, bp, ak, ap, mid, hi);
+    knuth_merge(c, bk, bp, ak, ap, lo, mid, hi);
+}
+
+/* counters (may be NULL): [0] = element moves (including the initial copy into
+ * the buffer), [1] = key comparisons.  Returns 0, or -1 on allocation failure. */
+int orc_knuthsort(uint64_t* keys, uint32_t* payload, int64_t n, int key_type, int order,
+                  int64_t* counters)
+{
+    orc_ctx c = { key_type, order, 0, 0 };
+    if (n >= 2) {
+        uint64_t* bk = (uint64_t*)malloc((size_t)n * sizeof(uint64_t));
+        uint32_t* bp = payload ? (uint32_t*)malloc((size_t)n * sizeof(uint32_t)) : NULL;
+        if (!bk || (payload && !bp)) { free(bk); free(bp); return -1; }
+        memcpy(bk, keys, (size_t)n * sizeof(uint64_t));
+        if (payload) memcpy(bp, payload, (size_t)n * sizeof(uint32_t));
+        c.moves += n;
+        knuth_rec(&c, keys, payload, bk, bp, 0, n);
+        free(bk); free(bp);
+    }
+    if (counters) { counters[0] = c.moves; counters[1] = c.compares; }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Frogsort: symmetric merging with <= 50% local buffer                       */
+/* ------------------------------------------------------------------------ */
+/*
+ * A node sorts n elements inside a region of n + b slots.  A "data-left" node
+ * ends with its data in the left n slots and its buffer on the right (Ab); a
+ * "data-right" node ends with buffer left, data right (aB).  The left child of
+ * every node is data-left and the right child data-right, so the two children's
+ * buffers meet in the middle of the parent's region.  The parent then merges
+ * from the inner ends of the two runs outward, and the result is aligned at the
+ * parent's outer border:
+ *   data-left parent : write from slot n-1 down to 0, larger key first; on ties
+ *                      the right run's element is written (it is later in the
+ *                      input, so it belongs at the higher slot).
+ *   data-right parent: write from slot b up to n+b-1, smaller key first; on ties
+ *                      the left run's element is written.
+ * The outer side of a data-left node is its left, of a data-right node its
+ * right.  Split rule: an odd surplus element goes to the outer child.  Buffer
+ * rule: the root has b = floor(n/2); the outer child gets floor(n_outer/2) and
+ * the inner child the rest of the parent's buffer.  (The paper gives only the
+ * root's buffer; this split reproduces both of its layout tables and gives
+ * every node at least as much buffer as its inner child has elements, which is
+ * what the in-place merge needs.)
+ *
+ * split_unit g: 1 = Frogsort1 (single-element splits); 2 = Frogsort0 (the
+ * triplet variant: a node of k triplets holds n = 2k elements and splits into
+ * ceil(k/2) outer and floor(k/2) inner triplets; a single triplet splits into
+ * its two elements).
+ */
+
+typedef struct {
+    int64_t n, b;       /* elements, buffer slots */
+    int64_t r;          /* first slot of the region */
+    int64_t s;          /* first input index of the node's elements */
+    int side;           /* 0 = data-left, 1 = data-right */
+    int depth;
+} frog_node;
+
+static void frog_children(const frog_node* p, int g, frog_node* L, frog_node* R)
+{
+    int64_t n_outer;
+    if (g == 2 && p->n >= 4 && p->n % 2 == 0) {
+        int64_t k = p->n / 2;
+        n_outer = 2 * ((k + 1) / 2);
+    } else {
+        n_outer = (p->n + 1) / 2;
+    }
+    int64_t n_inner = p->n - n_outer;
+    int64_t b_outer = n_outer / 2;
+    int64_t b_inner = p->b - b_outer;
+    L->side = 0; R->side = 1;
+    L->depth = R->depth = p->depth + 1;
+    if (p->side == 0) { L->n = n_outer; L->b = b_outer; R->n = n_inner; R->b = b_inner; }
+    else              { L->n = n_inner; L->b = b_inner; R->n = n_outer; R->b = b_outer; }
+    L->r = p->r;            R->r = p->r + L->n + L->b;
+    L->s = p->s;            R->s = p->s + L->n;
+}
+
+/* First slot of a node's data in its final layout. */
+static int64_t frog_data_slot(const frog_node* x)
+{
+    return x->side == 0 ? x->r : x->r + x->b;
+}
+
+/* Setup recursion: destination slot of every input element (its leaf's slot). */
+static void frog_setup_dest(const frog_node* x, int g, int64_t* dest)
+{
+    if (x->n == 1) { dest[x->s] = frog_data_slot(x); return; }
+    frog_node L, R;
+    frog_children(x, g, &L, &R);
+    frog_setup_dest(&L, g, dest);
+    frog_setup_dest(&R, g, dest);
+}
+
+typedef struct {
+    orc_ctx c;
+    int g;
+    int stop_depth;      /* merge only nodes with depth >= stop_depth */
+    uint64_t* k;         /* n + b slots */
+    uint32_t* p;         /* n + b slots or NULL */
+    int32_t* label;      /* optional: slot labels for the layout trace */
+} frog_run;
+
+static void frog_move(frog_run* f, int64_t to, int64_t from)
+{
+    f->k[to] = f->k[from];
+    if (f->p) f->p[to] = f->p[from];
+    if (f->label) f->label[to] = f->label[from];
+    f->c.moves++;
+}
+
+/* After a node's merge, the labels of its buffer slots are re-assigned: the
+ * buffer labels that were in the region are handed out to the free slots in
+ * increasing order (this is how the paper's tables print the buffer). */
+static void frog_relabel_buffer(frog_run* f, const frog_node* x, const int32_t* before)
+{
+    if (!f->label || x->b == 0) return;
+    int64_t nb = 0, m = x->n + x->b;
+    int32_t* bl = (int32_t*)malloc((size_t)x->b * sizeof(int32_t));
+    for (int64_t i = 0; i < m; i++)
+        if (before[i] < 0) bl[nb++] = before[i];
+    /* buffer labels are stored negative: -(position+1); increasing position
+     * order is decreasing stored value */
+    for (int64_t a = 0; a < nb; a++)
+        for (int64_t z = a + 1; z < nb; z++)
+            if (bl[z] > bl[a]) { int32_t t = bl[a]; bl[a] = bl[z]; bl[z] = t; }
+    int64_t b0 = x->side == 0 ? x->r + x->n : x->r;
+    for (int64_t i = 0; i < nb; i++) f->label[b0 + i] = bl[i];
+    free(bl);
+}
+
+static void frog_merge(frog_run* f, const frog_node* x, const frog_node* L, const frog_node* R)
+{
+    int kt = f->c.key_type, od = f->c.order;
+    int64_t m = x->n + x->b;
+    int32_t* before = NULL;
+    if (f->label) {
+        before = (int32_t*)malloc((size_t)m * sizeof(int32_t));
+        memcpy(before, f->label + x->r, (size_t)m * sizeof(int32_t));
+    }
+    int64_t la = frog_data_slot(L), lz = la + L->n;   /* left run  [la, lz) */
+    int64_t ra = frog_data_slot(R), rz = ra + R->n;   /* right run [ra, rz) */
+    if (x->side == 0) {
+        /* write downward from the inner end of the output [r, r+n) */
+        int64_t i = lz - 1, j = rz - 1, w = x->r + x->n - 1;
+        while (j >= ra) {
+            if (i < la) { frog_move(f, w--, j--); continue; }
+            f->c.compares++;
+            if (ord_cmp(f->k[j], f->k[i], kt, od) >= 0) frog_move(f, w--, j--);
+            else frog_move(f, w--, i--);
+        }
+        /* right run exhausted: the rest of the left run is already in place */
+    } else {
+        /* write upward from the inner end of the output [r+b, r+n+b) */
+        int64_t i = la, j = ra, w = x->r + x->b;
+        while (i < lz) {
+            if (j >= rz) { frog_move(f, w++, i++); continue; }
+            f->c.compares++;
+            if (ord_cmp(f->k[i], f->k[j], kt, od) <= 0) frog_move(f, w++, i++);
+            else frog_move(f, w++, j++);
+        }
+        /* left run exhausted: the rest of the right run is already in place */
+    }
+    if (f->label) {
+        /* mark every non-data slot of the region as buffer again */
+        int64_t d0 = frog_data_slot(x);
+        for (int64_t q = x->r; q < x->r + m; q++)
+            if (q < d0 || q >= d0 + x->n) f->label[q] = 0;
+        frog_relabel_buffer(f, x, before);
+        free(before);
+    }
+}
+
+static void frog_sort_rec(frog_run* f, const frog_node* x)
+{
+    if (x->n == 1) return;
+    frog_node L, R;
+    frog_children(x, f->g, &L, &R);
+    frog_sort_rec(f, &L);
+    frog_sort_rec(f, &R);
+    if (x->depth >= f->stop_depth) frog_merge(f, x, &L, &R);
+}
+
+static frog_node frog_root(int64_t n, int g)
+{
+    frog_node root;
+    root.n = n; root.b = n / 2; root.r = 0; root.s = 0; root.side = 0; root.depth = 0;
+    (void)g;
+    return root;
+}
+
+/* Buffer slots Frogsort needs for n elements (the paper's N/2). */
+int64_t orc_frog_buffer(int64_t n) { return n / 2; }
+
+/* Sort in place using n/2 extra slots.  counters (may be NULL): [0] setup moves,
+ * [1] merge moves, [2] merge comparisons.  split_unit 2 requires even n. */
+int orc_frogsort(uint64_t* keys, uint32_t* payload, int64_t n, int key_type, int order,
+                 int split_unit, int64_t* counters)
+{
+    if (split_unit == 2 && (n % 2)) return -2;
+    int64_t setup_moves = 0;
+    frog_run f;
+    memset(&f, 0, sizeof(f));
+    f.c.key_type = key_type; f.c.order = order; f.g = split_unit; f.stop_depth = 0;
+    if (n >= 2) {
+        int64_t b = n / 2, m = n + b;
+        f.k = (uint64_t*)malloc((size_t)m * sizeof(uint64_t));
+        f.p = payload ? (uint32_t*)malloc((size_t)m * sizeof(uint32_t)) : NULL;
+        int64_t* dest = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+        if (!f.k || (payload && !f.p) || !dest) { free(f.k); free(f.p); free(dest); return -1; }
+        /* the caller's n slots followed by the buffer's b slots */
+        memcpy(f.k, keys, (size_t)n * sizeof(uint64_t));
+        if (payload) memcpy(f.p, payload, (size_t)n * sizeof(uint32_t));
+        frog_node root = frog_root(n, split_unit);
+        frog_setup_dest(&root, split_unit, dest);
+        /* every element moves right (dest >= source) and dest increases with the
+         * source index, so moving from the highest element down never
+         * overwrites an element that has not moved yet */
+        for (int64_t e = n - 1; e >= 0; e--) {
+            if (dest[e] != e) {
+                f.k[dest[e]] = f.k[e];
+                if (payload) f.p[dest[e]] = f.p[e];
+                setup_moves++;
+            }
+        }
+        free(dest);
+        frog_sort_rec(&f, &root);
+        memcpy(keys, f.k, (size_t)n * sizeof(uint64_t));
+        if (payload) memcpy(payload, f.p, (size_t)n * sizeof(uint32_t));
+        free(f.k); free(f.p);
+    }
+    if (counters) { counters[0] = setup_moves; counters[1] = f.c.moves; counters[2] = f.c.compares; }
+    return 0;
+}
+
+/* Depth of the Frogsort tree for n elements (leaves are single elements). */
+static int frog_depth_rec(const frog_node* x, int g)
+{
+    if (x->n == 1) return x->depth;
+    frog_node L, R;
+    frog_children(x, g, &L, &R);
+    int a = frog_depth_rec(&L, g), z = frog_depth_rec(&R, g);
+    return a > z ? a : z;
+}
+
+int orc_frog_depth(int64_t n, int split_unit)
+{
+    frog_node root = frog_root(n, split_unit);
+    return n >= 1 ? frog_depth_rec(&root, split_unit) : 0;
+}
+
+/* Layout trace on presorted keys (key = setup slot), recording slot labels.
+ * labels_out has (D+1) rows of n + n/2 entries, D = depth of the deepest leaf:
+ * row 0 = after setup, row t = after the merges of every node at depth >= D - t
+ * (t merge levels, bottom-up).  A label is +(slot+1) for the data element
+ * that was set up in that slot, -(slot+1) for the buffer slot labelled by its
+ * setup slot.  Returns the number of rows, or -1. */
+int orc_frog_trace(int64_t n, int split_unit, int32_t* labels_out, int max_rows)
+{
+    if (n < 1 || (split_unit == 2 && (n % 2))) return -1;
+    int D = orc_frog_depth(n, split_unit);
+    if (D + 1 > max_rows) return -1;
+    int64_t b = n / 2, m = n + b;
+    frog_node root = frog_root(n, split_unit);
+    int64_t* dest = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+    frog_setup_dest(&root, split_unit, dest);
+    for (int row = 0; row <= D; row++) {
+        frog_run f;
+        memset(&f, 0, sizeof(f));
+        f.c.key_type = ORC_I64; f.c.order = ORC_ASC; f.g = split_unit;
+        f.stop_depth = D - row;   /* row t: merges at depths >= D - t */
+        f.k = (uint64_t*)calloc((size_t)m, sizeof(uint64_t));
+        f.label = (int32_t*)malloc((size_t)m * sizeof(int32_t));
+        char* is_data = (char*)calloc((size_t)m, 1);
+        for (int64_t e = 0; e < n; e++) is_data[dest[e]] = 1;
+        for (int64_t q = 0; q < m; q++) {
+            f.label[q] = is_data[q] ? (int32_t)(q + 1) : -(int32_t)(q + 1);
+            f.k[q] = (uint64_t)q;   /* presorted by setup slot */
+        }
+        if (row > 0) frog_sort_rec(&f, &root);
+        memcpy(labels_out + (size_t)row * (size_t)m, f.label, (size_t)m * sizeof(int32_t));
+        free(f.k); free(f.label); free(is_data);
+    }
+    free(dest);
+    return D + 1;
+}
