@@ -1,0 +1,383 @@
+"""Benchmark of the GB300 stable mergesort: one JSON line on stdout (rank 0).
+
+Default workload (one "step"): the plain GPU mergesort of 2^27 float64 keys with
+a uint32 index payload, four patterns from one seed (permuted uniform, heavy
+ties, ascending with 1% random transpositions, strictly descending), each at the
+100% and at the 50% buffer tier -- eight sorts per step, inputs resident in HBM
+(restored from pristine device copies, untimed, before each step; every sort's
+working set is 1.5 GiB, larger than L2).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the paper's own algorithms: Knuthsort
+for the 100% tier, Frogsort1 for the 50% tier) on a bounded sample of the same
+workload.  Multi-GPU runs (torchrun) are replicas: every rank sorts its own
+copy, no collective touches the data; value = all ranks' keys / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "stable sort Gkeys/s + HBM roofline fraction; learned/batched vs plain merge"
+UNIT = "Gkeys/s"
+N_FULL = 1 << 27
+TIERS = (1.0, 0.5)
+BYTES_PER_ELEM_PASS = 24      # 8 B key + 4 B payload, read and written once per pass
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_FULL, help="keys per sort (default 2^27)")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2402_01816_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.lines = []
+        self.dev = device_index
+
+    def __enter__(self):
+        try:
+            import torch
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(self.dev).uuid)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", uuid], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "note": "nvidia-smi unavailable"}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2402_01816_gb300 import inputs
+    sample = min(args.n, 1 << 20)
+    data = {p: inputs.make_keys(p, sample, seed=0) for p in inputs.PATTERNS_C1}
+    pay = inputs.index_payload(sample)
+
+    def step():
+        t = 0.0
+        for p in inputs.PATTERNS_C1:
+            for bf in TIERS:
+                t0 = time.perf_counter()
+                if bf >= 1.0:
+                    oracle.knuthsort(data[p], pay)
+                else:
+                    oracle.frogsort(data[p], pay)
+                t += time.perf_counter() - t0
+        return t
+
+    for _ in range(args.warmup):
+        step()
+    times = [step() for _ in range(args.steps)]
+    t = statistics.mean(times)
+    keys = sample * len(inputs.PATTERNS_C1) * len(TIERS)
+    v = keys / t / 1e9
+    desc = (f"CPU oracle (Knuthsort for the 100% tier, Frogsort1 for the 50% tier), single thread, "
+            f"{sample} keys per pattern x 4 patterns x 2 tiers per step")
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "plain stable mergesort, float64 keys + uint32 index payload, "
+                                   "patterns permut/ties/asc_noise/desc, 100% and 50% buffer",
+                       "n_per_sort": sample, "full_n": args.n},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def cpu_baseline(n_sample=1 << 22):
+    import oracle
+    from paper_2402_01816_gb300 import inputs
+    t, keys = 0.0, 0
+    for p in inputs.PATTERNS_C1:
+        k = inputs.make_keys(p, n_sample, seed=0)
+        pay = inputs.index_payload(n_sample)
+        t0 = time.perf_counter()
+        oracle.knuthsort(k, pay)
+        t += time.perf_counter() - t0
+        keys += n_sample
+    return {"value": keys / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle Knuthsort (100% buffer), single thread, {n_sample} keys of each of the 4 patterns "
+                      f"({keys} keys, {t:.1f} s)"}
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import paper_2402_01816_gb300 as g
+    from paper_2402_01816_gb300 import build as cuda_build
+    from paper_2402_01816_gb300 import inputs
+
+    if not os.path.exists(cuda_build.LIB):
+        cuda_build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    n = args.n
+    patterns = inputs.PATTERNS_C1
+    host = {p: inputs.make_keys(p, n, seed=0) for p in patterns}
+    pay_host = inputs.index_payload(n)
+    pristine = {p: torch.from_numpy(host[p]).to(dev) for p in patterns}
+    pay_pristine = torch.from_numpy(pay_host.view(np.int32)).to(dev)
+    combos = [(p, bf) for p in patterns for bf in TIERS]
+    work = {c: (torch.empty(n, dtype=torch.float64, device=dev), torch.empty(n, dtype=torch.int32, device=dev))
+            for c in combos}
+    stream = torch.cuda.current_stream()
+
+    def restore():
+        for (p, bf), (kt, pt) in work.items():
+            kt.copy_(pristine[p])
+            pt.copy_(pay_pristine)
+
+    def one_step(evs=None):
+        for i, c in enumerate(combos):
+            kt, pt = work[c]
+            if evs is not None:
+                evs[i][0].record(stream)
+            g.gns_sort(kt, pt, order=0, buffer_fraction=c[1], stream=stream)
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        restore()
+        one_step()
+    torch.cuda.synchronize()
+    if g.gns_stream_status() != 0:
+        raise RuntimeError("device status error during warm-up")
+
+    step_ms, per_combo = [], {c: [] for c in combos}
+    launches0 = g.gns_launch_count()
+    prof = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            restore()
+            torch.cuda.synchronize()
+            barrier()
+            g.gns_profile_read()          # drop records of earlier launches
+            g.gns_profile_enable(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in combos]
+            e0.record(stream)
+            one_step(evs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            g.gns_profile_enable(False)
+            barrier()
+            step_ms.append(e0.elapsed_time(e1))
+            for c, (a, b) in zip(combos, evs):
+                per_combo[c].append(a.elapsed_time(b))
+            prof.extend(g.gns_profile_read())
+    launches = g.gns_launch_count() - launches0
+    status = g.gns_stream_status()
+    if status != 0:
+        raise RuntimeError(f"device status {status} during the timed region")
+    clocks = clk.summary()
+
+    ms = statistics.mean(step_ms)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    keys_per_step = n * len(combos) * ws
+    value = keys_per_step / (ms / 1e3) / 1e9
+
+    # roofline of the dominant kernel (the 100% tier merge pass) and the others
+    peak, peak_kind = load_peaks()
+    by_kernel = {}
+    for name, t in prof:
+        by_kernel.setdefault(name, []).append(t)
+    total_kernel_ms = sum(sum(v) for v in by_kernel.values())
+
+    def roof(name):
+        if name not in by_kernel:
+            return None
+        avg = statistics.mean(by_kernel[name])
+        alg = BYTES_PER_ELEM_PASS * n
+        ach = alg / (avg / 1e3) / 1e9
+        return {"launches": len(by_kernel[name]), "avg_ms": avg, "algorithmic_bytes_per_launch": alg,
+                "achieved_gbs": ach, "frac": ach / peak,
+                "share": sum(by_kernel[name]) / total_kernel_ms if total_kernel_ms else None}
+
+    mp = roof("merge_pass")
+    roofline = {"bound": "hbm", "achieved": mp["achieved_gbs"] if mp else None, "peak": peak, "unit": "GB/s",
+                "frac": mp["frac"] if mp else None, "traffic": ncu_traffic("merge_pass"),
+                "kernel": "merge_pass (100% tier, one merge level over all n)",
+                "peak_source": f"{peak_kind} HBM copy bandwidth", "note": "frac is of measured peak"
+                if peak_kind == "measured" else "frac is of fallback peak"}
+    kernels = {}
+    for name in sorted(by_kernel):
+        r = roof(name) if name in ("merge_pass", "frog_merge", "tile_sort", "frog_setup") else None
+        kernels[name] = r or {"launches": len(by_kernel[name]), "avg_ms": statistics.mean(by_kernel[name]),
+                              "share": sum(by_kernel[name]) / total_kernel_ms if total_kernel_ms else None}
+
+    detail = {}
+    for c in combos:
+        t = statistics.mean(per_combo[c])
+        ram = (12 * n + g.gns_workspace_bytes(n, c[1])) / (12 * n)
+        detail[f"{c[0]}@{int(c[1] * 100)}%"] = {"ms": t, "gkeys_s": n / (t / 1e3) / 1e9, "pct_ram": ram,
+                                                "t_footprint_ms": ram * t}
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if rank == 0 or ws > 1:
+        hk = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+        hp = torch.empty(n, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+        e2e_times = []
+        for _ in range(max(1, args.e2e_steps)):
+            tot = 0.0
+            for (p, bf) in combos:
+                np.copyto(hk, host[p])
+                np.copyto(hp, pay_host)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                g.gns_sort_host(hk, hp, order=0, buffer_fraction=bf, stream=stream)
+                tot += time.perf_counter() - t0
+            e2e_times.append(tot)
+        te = statistics.mean(e2e_times)
+        e2e = {"value": n * len(combos) / te / 1e9 * ws, "unit": UNIT,
+               "h2d_bytes_per_step": n * 12 * len(combos), "d2h_bytes_per_step": n * 12 * len(combos),
+               "entry_point": "gns_sort_host (pinned host buffers, copies inside the timed call)"}
+
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu_baseline or ws > 1 else cpu_baseline()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "plain GPU mergesort, 2^27 float64 keys + uint32 index payload, "
+                                   "patterns permut/ties/asc_noise/desc, each at 100% and 50% buffer",
+                       "n_per_sort": n, "sorts_per_step": len(combos), "parallelism": f"replicas{ws}",
+                       "l2": "inputs larger than L2 (1.5 GiB per sort), no flush"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks, "kernels": kernels, "detail": detail}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * gns.h -- C ABI of the GB300-native stable mergesort after the greeNsort
+ * method (J. Oehlschlaegel, "Simple Symmetric Sustainable Sorting -- the
+ * greeNsort article", arXiv 2402.01816).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named keys / payload / offsets are DEVICE pointers owned by the
+ *   caller (except in gns_sort_host, which takes host pointers).  Sorting is in
+ *   place: on return (stream-ordered) keys[0..n) and payload[0..n) hold the
+ *   sorted sequence.  keys and payload must not overlap.
+ * - Keys are 64-bit (float64 or int64, 8-byte aligned); payloads are uint32
+ *   (4-byte aligned).  payload may be NULL (keys only).
+ * - Result: the unique stable sort ("Definition of sorting" chapter: the
+ *   AscLeft and DescLeft API targets): keys in order from left to right, equal
+ *   keys in their input order, for both orders.  DescLeft is not the reverse of
+ *   AscLeft: ties keep input order in both.  The key bit patterns are moved,
+ *   never canonicalised.
+ * - float64 order: IEEE 754 totalOrder: -NaN < -inf < ... < -0.0 < +0.0 < ...
+ *   < +inf < +NaN (NaNs by payload bits).  -0.0 and +0.0 are distinct keys.
+ * - Calls are asynchronous and ordered on `stream` like CUDA calls.  Errors the
+ *   host can see (bad arguments, allocation failure, launch failure) are
+ *   returned at once.  Errors found on the device (a bounded wait that ran
+ *   out) land in a per-device status word read by gns_stream_status().  With
+ *   the environment variable GNS_SYNC_STATUS=1 every call synchronises its
+ *   stream and returns that status itself.
+ * - Workspace: the library allocates only its own scratch, through the
+ *   allocator hook (gns_set_allocator; default cudaMallocAsync on `stream`) and
+ *   frees it stream-ordered before returning.  gns_workspace_bytes() reports
+ *   the size, so %RAM = (12 n + workspace) / 12 n (Sustainability measures
+ *   section).
+ */
+#ifndef GNS_H
+#define GNS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL = the legacy default stream. */
+typedef struct CUstream_st* gns_stream_t;
+
+/* Return codes (never exceptions). */
+enum {
+    GNS_OK = 0,
+    GNS_ERR_INVALID = -1,      /* bad argument; nothing was launched          */
+    GNS_ERR_UNSUPPORTED = -2,  /* valid request this library does not serve  */
+    GNS_ERR_OOM = -3,          /* the allocator returned NULL                 */
+    GNS_ERR_CUDA = -4,         /* a CUDA runtime call or launch failed        */
+    GNS_ERR_TIMEOUT = -5       /* a device-side bounded wait ran out          */
+};
+
+/* Sort orders: the two stable API targets served (AscLeft, DescLeft). */
+enum { GNS_ASCENDING = 0, GNS_DESCENDING = 1 };
+
+/* Key types. */
+enum { GNS_KEY_F64 = 0, GNS_KEY_I64 = 1 };
+
+/* Workspace kinds for gns_workspace_bytes. */
+enum { GNS_WS_SORT = 0, GNS_WS_LEARNED = 1 };
+
+/*
+ * gns_sort -- stable in-place sort of n float64 keys with uint32 payloads.
+ *
+ * Method: divide & conquer mergesort ("Merging or partitioning?" chapter:
+ * split & merge, most work in the merge phases).  Tiles of up to 4096
+ * elements are sorted in shared memory; then every merge level is one pass
+ * over HBM, split evenly across CTAs by merge-path co-rank search (the
+ * "Parallel" section's binary merge over any number of workers).  Before
+ * sorting, one read pass detects presorted input (Omitsort / Octosort,
+ * "Full adaptivity" section): non-decreasing input is left untouched, strictly
+ * decreasing input is reversed once.
+ *
+ * buffer_fraction selects the memory tier:
+ *   >= 1.0      100% distant buffer: Nocopy ping-pong between the keys and an
+ *               n-element buffer, the last pass landing in keys ("Forgotten
+ *               art": Knuthsort).  Workspace ~ 12 n bytes.
+ *   [0.5, 1.0)  <= 50% local buffer: Frogsort1 layout ("Symmetric merging",
+ *               "Frogsort1" sections): floor(n/2) buffer slots appended to
+ *               the data, left branches data-left, right branches data-right,
+ *               merges from the inner ends outward, in place.  Workspace ~ 6 n
+ *               bytes.
+ *   < 0.5, NaN  GNS_ERR_UNSUPPORTED (< 0.5) / GNS_ERR_INVALID (NaN, negative).
+ *
+ * Arguments: keys (device, n float64), payload (device, n uint32, or NULL),
+ * n >= 0 (n == 0 and n == 1 are no-ops), order GNS_ASCENDING/GNS_DESCENDING.
+ * Errors: GNS_ERR_INVALID for n < 0, keys == NULL with n > 0, misaligned
+ * pointers, an unknown order; GNS_ERR_OOM; GNS_ERR_CUDA.
+ */
+int gns_sort(double* keys, uint32_t* payload, int64_t n, int order,
+             double buffer_fraction, gns_stream_t stream);
+
+/* gns_sort for int64 keys (two's complement order). */
+int gns_sort_i64(int64_t* keys, uint32_t* payload, int64_t n, int order,
+                 double buffer_fraction, gns_stream_t stream);
+
+/*
+ * gns_sort_host -- the same sort on HOST arrays: copies keys and payload to
+ * the device on `stream`, sorts them there, copies them back and synchronises
+ * the stream.  key_type is GNS_KEY_F64 or GNS_KEY_I64.  Host arrays should be
+ * pinned for full copy bandwidth (pageable memory works, slower).  The device
+ * copies are workspace (allocator hook).  Errors as gns_sort; the device
+ * status word is checked before returning.
+ */
+int gns_sort_host(void* keys_host, uint32_t* payload_host, int64_t n, int key_type,
+                  int order, double buffer_fraction, gns_stream_t stream);
+
+/*
+ * gns_segmented_sort -- stable ascending sort of every segment
+ * [offsets[s], offsets[s+1]) of an int64 key array independently, in place.
+ * No counterpart in the paper (a batching form of the same mergesort): every
+ * segment is sorted by the same tile sort and merge passes; segments longer
+ * than a tile get only as many merge levels as they need, and each segment's
+ * last level lands in keys (the Omitsort idea of the "Full adaptivity" section:
+ * the merge decides where the data lies).
+ *
+ * offsets: device int64[nseg + 1], offsets[0] == 0, non-decreasing (empty
+ * segments allowed), offsets[nseg] = total length; not validated on the
+ * device.  nseg >= 0.  The whole call is one CUDA-graph launch after its first
+ * use for a given (nseg, total length, pointers, stream) -- the graph is
+ * captured once and replayed.
+ */
+int gns_segmented_sort(int64_t* keys, uint32_t* payload, const int64_t* offsets,
+                       int64_t nseg, gns_stream_t stream);
+
+/* gns_segmented_sort with a key type and order.  total_n = offsets[nseg] must
+ * be passed by the caller (the host never reads device offsets). */
+int gns_segmented_sort_ex(void* keys, int key_type, uint32_t* payload,
+                          const int64_t* offsets, int64_t nseg, int64_t total_n,
+                          int order, gns_stream_t stream);
+
+/* Size in bytes of the scratch a call allocates.  kind = GNS_WS_SORT for
+ * gns_sort at this buffer_fraction, GNS_WS_LEARNED for gns_learned_sort. */
+size_t gns_workspace_bytes(int64_t n, double buffer_fraction, int kind);
+
+/*
+ * Allocator hook for the library's scratch.  alloc(bytes, stream, ctx) returns
+ * device memory usable in stream order on `stream` (or NULL -> GNS_ERR_OOM);
+ * free(ptr, stream, ctx) releases it in stream order.  Passing NULL for both
+ * restores the default (cudaMallocAsync / cudaFreeAsync).  Process-wide; not
+ * to be changed while calls are in flight.
+ */
+typedef void* (*gns_alloc_fn)(size_t bytes, gns_stream_t stream, void* ctx);
+typedef void (*gns_free_fn)(void* ptr, gns_stream_t stream, void* ctx);
+void gns_set_allocator(gns_alloc_fn alloc, gns_free_fn free_fn, void* ctx);
+
+/* Synchronises `stream`, returns the current device's status word (GNS_OK or
+ * the first device-side error since the last read) and clears it. */
+int gns_stream_status(gns_stream_t stream);
+
+/* Static description of a return code. */
+const char* gns_strerror(int code);
+
+/* Library version string. */
+const char* gns_version(void);
+
+/* --- instrumentation (used by the benchmark; no effect on results) -------- */
+
+/* Number of kernels this library has launched in this process. */
+uint64_t gns_launch_count(void);
+
+/* When on (1), every kernel launch is bracketed by CUDA events on its stream;
+ * gns_profile_read copies up to `cap` records (kernel id, milliseconds) of the
+ * launches since the last read, after synchronising their streams, and returns
+ * how many there were.  gns_kernel_name maps an id to its kernel's name. */
+void gns_profile_enable(int on);
+int gns_profile_read(int* kernel_ids, float* ms, int cap);
+const char* gns_kernel_name(int kernel_id);
+
+/* Bounded device waits: the spin limit in nanoseconds (default 2 s) after which
+ * a waiting CTA records GNS_ERR_TIMEOUT and returns without writing.  The
+ * debug fault `skip_publish_ticket` (>= 0) makes the CTA holding that ticket of
+ * the next in-place merge skip publishing its "inputs loaded" flag, so that the
+ * wait of the next CTA runs out (used to test the timeout path; -1 = off). */
+void gns_set_wait_limit_ns(uint64_t ns);
+void gns_debug_skip_publish(int64_t ticket);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GNS_H */

@@ -1,2 +1,13 @@
-"""GB300-native stable mergesort after the greeNsort method (placeholder; the
-binding is added with the CUDA library)."""
+"""GB300-native stable mergesort after the greeNsort method (arXiv 2402.01816).
+
+The sorting runs in the CUDA library ``_build/libgns.so`` (sources in
+``csrc/``, C ABI in ``include/gns.h``); this package only builds it
+(``build.build()``) and binds it (``_native``): the Python functions carry the
+C entry points' names and do argument marshalling only.  ``inputs`` holds the
+seeded synthetic workloads.
+"""
+from ._native import (ASCENDING, DESCENDING, GNS_ERR_CUDA, GNS_ERR_INVALID, GNS_ERR_OOM,  # noqa: F401
+                      GNS_ERR_TIMEOUT, GNS_ERR_UNSUPPORTED, GNS_OK, GnsError, gns_debug_skip_publish,
+                      gns_launch_count, gns_profile_enable, gns_profile_read, gns_segmented_sort,
+                      gns_set_wait_limit_ns, gns_sort, gns_sort_host, gns_stream_status, gns_version,
+                      gns_workspace_bytes, lib)

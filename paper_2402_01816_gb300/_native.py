@@ -1,0 +1,190 @@
+"""ctypes binding of libgns.so -- argument marshalling only.
+
+Every function has the name of the C entry point it calls (include/gns.h) and
+does nothing but check tensor types, take raw pointers and the current CUDA
+stream, call the library and turn a non-zero return code into an exception.
+There is no fallback: if the compiled library is missing the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libgns.so")
+
+GNS_OK, GNS_ERR_INVALID, GNS_ERR_UNSUPPORTED, GNS_ERR_OOM, GNS_ERR_CUDA, GNS_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+ASCENDING, DESCENDING = 0, 1
+KEY_F64, KEY_I64 = 0, 1
+WS_SORT, WS_LEARNED = 0, 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class GnsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+def lib() -> ctypes.CDLL:
+    """Load libgns.so (built by paper_2402_01816_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                                   "(run paper_2402_01816_gb300.build.build())")
+            L = ctypes.CDLL(LIB_PATH)
+            P, i64, i32, u64, f64 = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                     ctypes.c_uint64, ctypes.c_double)
+            sig = {
+                "gns_sort": ([P, P, i64, i32, f64, P], i32),
+                "gns_sort_i64": ([P, P, i64, i32, f64, P], i32),
+                "gns_sort_host": ([P, P, i64, i32, i32, f64, P], i32),
+                "gns_segmented_sort": ([P, P, P, i64, P], i32),
+                "gns_segmented_sort_ex": ([P, i32, P, P, i64, i64, i32, P], i32),
+                "gns_workspace_bytes": ([i64, f64, i32], ctypes.c_size_t),
+                "gns_set_allocator": ([P, P, P], None),
+                "gns_stream_status": ([P], i32),
+                "gns_strerror": ([i32], ctypes.c_char_p),
+                "gns_version": ([], ctypes.c_char_p),
+                "gns_launch_count": ([], u64),
+                "gns_profile_enable": ([i32], None),
+                "gns_profile_read": ([P, P, i32], i32),
+                "gns_kernel_name": ([i32], ctypes.c_char_p),
+                "gns_set_wait_limit_ns": ([u64], None),
+                "gns_debug_skip_publish": ([i64], None),
+            }
+            for name, (args, res) in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().gns_strerror(code).decode()
+    except RuntimeError:
+        return f"error {code}"
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != GNS_OK:
+        raise GnsError(rc, where)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dev_ptr(t, dtype, name):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def gns_sort(keys, payload=None, order: int = ASCENDING, buffer_fraction: float = 1.0, stream=None) -> None:
+    """In-place stable sort of a CUDA float64 or int64 tensor (+ uint32 payload
+    passed as an int32 tensor, reinterpreted bit for bit)."""
+    import torch
+    n = keys.numel()
+    if payload is not None and payload.numel() != n:
+        raise ValueError("payload must have as many elements as keys")
+    if keys.dtype == torch.float64:
+        fn, kd = lib().gns_sort, torch.float64
+    elif keys.dtype == torch.int64:
+        fn, kd = lib().gns_sort_i64, torch.int64
+    else:
+        raise TypeError("keys must be float64 or int64")
+    _check(fn(_dev_ptr(keys, kd, "keys"), _dev_ptr(payload, torch.int32, "payload"), n, order,
+              float(buffer_fraction), _stream(stream)), "gns_sort")
+
+
+def gns_sort_host(keys: np.ndarray, payload: np.ndarray | None = None, order: int = ASCENDING,
+                  buffer_fraction: float = 1.0, stream=None) -> None:
+    """Same sort on host arrays (copied to the device and back inside the call)."""
+    if keys.dtype == np.float64:
+        kt = KEY_F64
+    elif keys.dtype == np.int64:
+        kt = KEY_I64
+    else:
+        raise TypeError("keys must be float64 or int64")
+    if not keys.flags.c_contiguous or (payload is not None and not payload.flags.c_contiguous):
+        raise ValueError("arrays must be C-contiguous")
+    if payload is not None and (payload.dtype != np.uint32 or payload.size != keys.size):
+        raise TypeError("payload must be uint32 with as many elements as keys")
+    pp = None if payload is None else ctypes.c_void_p(payload.ctypes.data)
+    _check(lib().gns_sort_host(ctypes.c_void_p(keys.ctypes.data), pp, keys.size, kt, order,
+                               float(buffer_fraction), _stream(stream)), "gns_sort_host")
+
+
+def gns_segmented_sort(keys, payload, offsets, order: int = ASCENDING, stream=None) -> None:
+    """Stable sort of every segment [offsets[s], offsets[s+1]) independently."""
+    import torch
+    if keys.dtype == torch.int64:
+        kt = KEY_I64
+    elif keys.dtype == torch.float64:
+        kt = KEY_F64
+    else:
+        raise TypeError("keys must be int64 or float64")
+    nseg = offsets.numel() - 1
+    if nseg < 0:
+        raise ValueError("offsets needs nseg + 1 entries")
+    _check(lib().gns_segmented_sort_ex(_dev_ptr(keys, keys.dtype, "keys"), kt,
+                                       _dev_ptr(payload, torch.int32, "payload"),
+                                       _dev_ptr(offsets, torch.int64, "offsets"), nseg, keys.numel(),
+                                       order, _stream(stream)), "gns_segmented_sort")
+
+
+def gns_workspace_bytes(n: int, buffer_fraction: float = 1.0, kind: int = WS_SORT) -> int:
+    return int(lib().gns_workspace_bytes(n, float(buffer_fraction), kind))
+
+
+def gns_stream_status(stream=None) -> int:
+    return int(lib().gns_stream_status(_stream(stream)))
+
+
+def gns_version() -> str:
+    return lib().gns_version().decode()
+
+
+def gns_launch_count() -> int:
+    return int(lib().gns_launch_count())
+
+
+def gns_profile_enable(on: bool) -> None:
+    lib().gns_profile_enable(1 if on else 0)
+
+
+def gns_profile_read(cap: int = 1 << 16):
+    """[(kernel name, milliseconds)] of the launches since the last read."""
+    ids = np.zeros(cap, dtype=np.int32)
+    ms = np.zeros(cap, dtype=np.float32)
+    n = lib().gns_profile_read(ctypes.c_void_p(ids.ctypes.data), ctypes.c_void_p(ms.ctypes.data), cap)
+    n = min(n, cap)
+    return [(lib().gns_kernel_name(int(i)).decode(), float(t)) for i, t in zip(ids[:n], ms[:n])]
+
+
+def gns_set_wait_limit_ns(ns: int) -> None:
+    lib().gns_set_wait_limit_ns(int(ns))
+
+
+def gns_debug_skip_publish(ticket: int) -> None:
+    lib().gns_debug_skip_publish(int(ticket))

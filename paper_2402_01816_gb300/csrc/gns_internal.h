@@ -1,0 +1,86 @@
+// gns_internal.h -- host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "../../include/gns.h"
+
+namespace gns {
+
+// Kernel ids for instrumentation (gns_profile_read / gns_kernel_name).
+enum KernelId {
+    K_RUN_DETECT = 0,
+    K_REVERSE,
+    K_TILE_SORT,
+    K_MERGE_PARTITION,
+    K_MERGE_PASS,
+    K_FROG_PLAN,
+    K_FROG_SETUP,
+    K_FROG_PARTITION,
+    K_FROG_MERGE,
+    K_ERR_PUBLISH,
+    K_SEG_PLAN,
+    K_SEG_TILE,
+    K_SEG_MERGE,
+    K_LEARN_SAMPLE,
+    K_LEARN_FIT,
+    K_LEARN_SPLIT,
+    K_LEARN_HIST,
+    K_LEARN_SCAN,
+    K_LEARN_SCATTER,
+    K_LEARN_VERIFY,
+    K_MLP_FWD,
+    K_MLP_BWD,
+    K_MLP_ADAM,
+    K_NOALLOC_SORT,
+    K_COUNT
+};
+
+// Launch bookkeeping: count every launch; when profiling is on, bracket it by
+// events on its stream.
+void prof_before(int kid, cudaStream_t s);
+void prof_after(cudaStream_t s);
+extern std::atomic<uint64_t> g_launches;
+
+template <typename Kernel, typename... Args>
+inline cudaError_t launch(int kid, Kernel kernel, dim3 grid, dim3 block, size_t smem,
+                          cudaStream_t s, Args... args)
+{
+    if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
+    prof_before(kid, s);
+    kernel<<<grid, block, smem, s>>>(args...);
+    cudaError_t e = cudaGetLastError();
+    prof_after(s);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return e;
+}
+
+// Device address of the per-device status word (resolved once per device).
+int* status_word_ptr();
+
+// Scratch allocation through the allocator hook.
+void* ws_alloc(size_t bytes, cudaStream_t s);
+void ws_free(void* p, cudaStream_t s);
+
+// Spin limit of bounded device waits, and the debug fault switch.
+uint64_t wait_limit_ns();
+int64_t take_debug_skip_publish();   // returns the ticket (or -1) and clears it
+
+// Folds a call's error word into the per-device status word (one tiny kernel).
+cudaError_t publish_call_error(const int* call_err, cudaStream_t s);
+
+// GNS_SYNC_STATUS=1: synchronise and return the status word after each call.
+int finish_call(int rc, cudaStream_t s);
+
+// Rounds a byte count up to 256 (every workspace sub-buffer starts aligned).
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// gns_sort core: keys are raw 64-bit patterns, mode = key type | order bits.
+int sort_device(uint64_t* keys, uint32_t* payload, int64_t n, int mode,
+                double buffer_fraction, cudaStream_t s);
+size_t sort_workspace_bytes(int64_t n, double buffer_fraction);
+
+}  // namespace gns

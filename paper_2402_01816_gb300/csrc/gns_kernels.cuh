@@ -1,0 +1,571 @@
+// gns_kernels.cuh -- the mergesort hot path on sm_103a.
+//
+//  tile sort        stable sort of a 4096-element tile in registers + shared memory:
+//                   each thread sorts 16 keys with an odd-even transposition network
+//                   (adjacent strict swaps only, hence stable), then 8 rounds of
+//                   pairwise merges in shared memory, each thread finding its
+//                   16-output slice by a merge-path co-rank search.
+//  run detection    one read pass deciding "already in order" / "strictly reversed"
+//                   (Omitsort / Octosort adaptivity, "Full adaptivity" section).
+//  merge partition  merge-path co-rank of every CTA's first output, so that every
+//                   merge level is split evenly over any number of CTAs (the
+//                   "Parallel" section's binary merge over an arbitrary number of
+//                   workers).
+//  merge pass       one merge level: each CTA loads its two input slices to shared
+//                   memory, merges 16 outputs per thread, stores coalesced.
+//  frog kernels     the <= 50% buffer tier: the Frogsort1 layout ("Symmetric
+//                   merging", "Frogsort1" sections) with a fused setup (tile sort +
+//                   scatter to the gapped leaf slots) and in-place merge levels.
+//
+// All comparisons are on encoded keys (gns_device.cuh): one unsigned compare.
+// Ties: the left run always wins, which makes every merge stable.
+#pragma once
+
+#include "gns_device.cuh"
+
+namespace gns {
+
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 16;
+constexpr int TILE = SORT_THREADS * SORT_ITEMS;       // 4096 elements
+constexpr int MERGE_THREADS = 256;
+constexpr int MERGE_ITEMS = 16;
+constexpr int CHUNK = MERGE_THREADS * MERGE_ITEMS;    // 4096 outputs per CTA
+constexpr int DETECT_TILE = 4096;
+
+// Shared-memory index with one pad slot per 16 elements: thread t's blocked
+// element j sits at 17 t + j, so a warp's blocked accesses hit distinct banks.
+__device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
+
+template <int N>
+struct SmemKV {
+    uint64_t k[N + N / 16];
+    uint32_t v[N + N / 16];
+};
+
+// Number of A elements among the first `diag` outputs of the stable merge of
+// A[0, na) and B[0, nb), left run winning ties.
+template <typename GA, typename GB>
+__device__ __forceinline__ int64_t merge_path(int64_t diag, int64_t na, int64_t nb, GA A, GB B)
+{
+    int64_t lo = imax64(0, diag - nb), hi = imin64(diag, na);
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (A(mid) <= B(diag - 1 - mid)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Serial stable merge of ITEMS outputs from shared-memory runs [i, ie) and
+// [j, je) into registers.  Reads past the end are clamped to `last`.
+template <int N, int ITEMS>
+__device__ __forceinline__ void serial_merge(const SmemKV<N>& sm, int i, int ie, int j, int je,
+                                             int last, uint64_t (&k)[ITEMS], uint32_t (&v)[ITEMS])
+{
+    uint64_t ka = i < ie ? sm.k[pidx(i)] : ~0ull;
+    uint64_t kb = j < je ? sm.k[pidx(j)] : ~0ull;
+#pragma unroll
+    for (int x = 0; x < ITEMS; ++x) {
+        bool takeA = (j >= je) || (i < ie && ka <= kb);
+        int src = takeA ? i : j;
+        k[x] = takeA ? ka : kb;
+        v[x] = sm.v[pidx(src < last ? src : last)];
+        if (takeA) {
+            ++i;
+            ka = i < ie ? sm.k[pidx(i)] : ~0ull;
+        } else {
+            ++j;
+            kb = j < je ? sm.k[pidx(j)] : ~0ull;
+        }
+    }
+}
+
+// Stable sort of the tile held in shared memory at logical positions [0, T).
+// Positions >= n_valid must hold the maximal key ~0 (they stay behind every
+// real element: equal keys keep position order).  On return the sorted tile is
+// at logical positions [0, n_valid) of `sm`.
+template <int THREADS, int ITEMS>
+__device__ void block_sort_smem(SmemKV<THREADS * ITEMS>& sm, int n_valid)
+{
+    constexpr int T = THREADS * ITEMS;
+    const int t = threadIdx.x;
+    uint64_t k[ITEMS];
+    uint32_t v[ITEMS];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        k[j] = sm.k[pidx(t * ITEMS + j)];
+        v[j] = sm.v[pidx(t * ITEMS + j)];
+    }
+    // odd-even transposition network: ITEMS phases of adjacent compare-swaps
+#pragma unroll
+    for (int ph = 0; ph < ITEMS; ++ph) {
+#pragma unroll
+        for (int j = ph & 1; j + 1 < ITEMS; j += 2) {
+            if (k[j + 1] < k[j]) {
+                uint64_t tk = k[j]; k[j] = k[j + 1]; k[j + 1] = tk;
+                uint32_t tv = v[j]; v[j] = v[j + 1]; v[j + 1] = tv;
+            }
+        }
+    }
+    for (int w = ITEMS; w < T && w < n_valid; w <<= 1) {
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            sm.k[pidx(t * ITEMS + j)] = k[j];
+            sm.v[pidx(t * ITEMS + j)] = v[j];
+        }
+        __syncthreads();
+        const int gthreads = (2 * w) / ITEMS;
+        const int a_beg = (t / gthreads) * 2 * w;
+        const int b_beg = a_beg + w;
+        const int diag = (t % gthreads) * ITEMS;
+        int ai = (int)merge_path(
+            diag, w, w, [&](int64_t x) { return sm.k[pidx(a_beg + (int)x)]; },
+            [&](int64_t x) { return sm.k[pidx(b_beg + (int)x)]; });
+        serial_merge<T, ITEMS>(sm, a_beg + ai, b_beg, b_beg + diag - ai, b_beg + w, T - 1, k, v);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        sm.k[pidx(t * ITEMS + j)] = k[j];
+        sm.v[pidx(t * ITEMS + j)] = v[j];
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Run detection and reversal
+// ---------------------------------------------------------------------------
+
+// presorted[0]: every adjacent pair non-decreasing (under the call's order);
+// presorted[1]: every adjacent pair strictly decreasing.  Both start at 1; any
+// CTA finding a violation clears the flag.  CTAs that start after both flags are
+// cleared return without reading (random inputs cost about one wave).
+__global__ void __launch_bounds__(256) run_detect_kernel(const uint64_t* __restrict__ keys, int64_t n,
+                                                         int mode, int* presorted)
+{
+    if (ld_relaxed(&presorted[0]) == 0 && ld_relaxed(&presorted[1]) == 0) return;
+    const int64_t base = (int64_t)blockIdx.x * DETECT_TILE;
+    const int64_t end = imin64(base + DETECT_TILE, n);
+    bool asc = true, desc = true;
+    for (int64_t i = base + threadIdx.x; i < end; i += blockDim.x) {
+        if (i == 0) continue;
+        uint64_t x = encode_key(keys[i - 1], mode), y = encode_key(keys[i], mode);
+        asc &= (x <= y);
+        desc &= (x > y);
+    }
+    asc = __syncthreads_and(asc);
+    desc = __syncthreads_and(desc);
+    if (threadIdx.x == 0) {
+        if (!asc) atomicAnd(&presorted[0], 0);
+        if (!desc) atomicAnd(&presorted[1], 0);
+    }
+}
+
+// Reverses a strictly decreasing array in place (Octosort's final reversal: the
+// reverse of a strictly ordered run is the stable sort, as it has no ties).
+__global__ void reverse_kernel(uint64_t* keys, uint32_t* vals, int64_t n, const int* presorted)
+{
+    if (presorted[0] != 0 || presorted[1] == 0) return;
+    const int64_t half = n / 2;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < half;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = n - 1 - i;
+        uint64_t a = keys[i], b = keys[j];
+        keys[i] = b; keys[j] = a;
+        if (vals) {
+            uint32_t x = vals[i], y = vals[j];
+            vals[i] = y; vals[j] = x;
+        }
+    }
+}
+
+__device__ __forceinline__ bool skip_all(const int* presorted)
+{
+    return presorted != nullptr && (presorted[0] | presorted[1]) != 0;
+}
+
+// ---------------------------------------------------------------------------
+// 100% tier: tile sort, partition, ping-pong merge pass
+// ---------------------------------------------------------------------------
+
+// Sorts tile blockIdx.x of src (raw keys) into dst (encoded keys, or raw when
+// this is the only pass).  src == dst is allowed (each CTA owns its tile).
+template <int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS)
+    tile_sort_kernel(const uint64_t* src_k, const uint32_t* src_v, uint64_t* dst_k, uint32_t* dst_v,
+                     int64_t n, int mode, int decode_out, const int* presorted)
+{
+    constexpr int T = THREADS * ITEMS;
+    if (skip_all(presorted)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemKV<T>& sm = *reinterpret_cast<SmemKV<T>*>(smem_raw);
+    const int t = threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * T;
+    const int nv = (int)imin64(T, n - base);
+#pragma unroll 4
+    for (int j = 0; j < ITEMS; ++j) {
+        int i = t + j * THREADS;
+        int64_t g = base + i;
+        bool ok = i < nv;
+        sm.k[pidx(i)] = ok ? encode_key(src_k[g], mode) : ~0ull;
+        sm.v[pidx(i)] = (ok && src_v) ? src_v[g] : 0u;
+    }
+    block_sort_smem<THREADS, ITEMS>(sm, nv);
+#pragma unroll 4
+    for (int j = 0; j < ITEMS; ++j) {
+        int i = t + j * THREADS;
+        if (i < nv) {
+            uint64_t key = sm.k[pidx(i)];
+            dst_k[base + i] = decode_out ? decode_key(key, mode) : key;
+            if (dst_v) dst_v[base + i] = sm.v[pidx(i)];
+        }
+    }
+}
+
+// splits[b] = co-rank (A elements) of output position b*CHUNK within its pair of
+// runs of width w.
+__global__ void merge_partition_kernel(const uint64_t* __restrict__ k, int64_t n, int64_t w,
+                                       int64_t nblocks, int64_t* splits, const int* presorted)
+{
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nblocks || skip_all(presorted)) return;
+    int64_t out0 = b * CHUNK;
+    int64_t ps = (out0 / (2 * w)) * (2 * w);
+    int64_t lenA = imin64(w, n - ps);
+    int64_t lenB = imax64(0, imin64(w, n - ps - w));
+    const uint64_t* A = k + ps;
+    const uint64_t* B = k + ps + lenA;
+    splits[b] = merge_path(out0 - ps, lenA, lenB, [&](int64_t x) { return A[x]; },
+                           [&](int64_t x) { return B[x]; });
+}
+
+// One Nocopy merge level: runs of width w in src merged pairwise into dst.
+template <int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS)
+    merge_pass_kernel(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sv,
+                      uint64_t* __restrict__ dk, uint32_t* __restrict__ dv, int64_t n, int64_t w,
+                      const int64_t* __restrict__ splits, int mode, int decode_out,
+                      const int* presorted)
+{
+    constexpr int C = THREADS * ITEMS;
+    if (skip_all(presorted)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemKV<C>& sm = *reinterpret_cast<SmemKV<C>*>(smem_raw);
+    const int t = threadIdx.x;
+    const int64_t b = blockIdx.x;
+    const int64_t out0 = b * C;
+    const int64_t ps = (out0 / (2 * w)) * (2 * w);
+    const int64_t lenA = imin64(w, n - ps);
+    const int64_t lenB = imax64(0, imin64(w, n - ps - w));
+    const int64_t tot = lenA + lenB;
+    const int64_t d0 = out0 - ps, d1 = imin64(d0 + C, tot);
+    const int64_t a0 = splits[b];
+    const int64_t a1 = (d1 == tot) ? lenA : splits[b + 1];
+    const int na = (int)(a1 - a0), nb = (int)((d1 - a1) - (d0 - a0));
+    const int cnt = na + nb;
+    const uint64_t* A = sk + ps + a0;
+    const uint64_t* B = sk + ps + lenA + (d0 - a0);
+    const uint32_t* Av = sv ? sv + ps + a0 : nullptr;
+    const uint32_t* Bv = sv ? sv + ps + lenA + (d0 - a0) : nullptr;
+#pragma unroll 4
+    for (int j = 0; j < ITEMS; ++j) {
+        int i = t + j * THREADS;
+        if (i < cnt) {
+            bool fa = i < na;
+            sm.k[pidx(i)] = fa ? A[i] : B[i - na];
+            sm.v[pidx(i)] = sv ? (fa ? Av[i] : Bv[i - na]) : 0u;
+        }
+    }
+    __syncthreads();
+    uint64_t k[ITEMS];
+    uint32_t v[ITEMS];
+    const int diag = t * ITEMS;
+    if (diag < cnt) {
+        int ai = (int)merge_path(
+            diag, na, nb, [&](int64_t x) { return sm.k[pidx((int)x)]; },
+            [&](int64_t x) { return sm.k[pidx(na + (int)x)]; });
+        serial_merge<C, ITEMS>(sm, ai, na, na + diag - ai, cnt, cnt - 1, k, v);
+    }
+    __syncthreads();
+    if (diag < cnt) {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            if (diag + j < cnt) {
+                sm.k[pidx(diag + j)] = k[j];
+                sm.v[pidx(diag + j)] = v[j];
+            }
+        }
+    }
+    __syncthreads();
+    uint64_t* D = dk + out0;
+    uint32_t* Dv = dv ? dv + out0 : nullptr;
+#pragma unroll 4
+    for (int j = 0; j < ITEMS; ++j) {
+        int i = t + j * THREADS;
+        if (i < cnt) {
+            uint64_t key = sm.k[pidx(i)];
+            D[i] = decode_out ? decode_key(key, mode) : key;
+            if (Dv) Dv[i] = sm.v[pidx(i)];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// <= 50% tier: the Frogsort1 layout
+// ---------------------------------------------------------------------------
+//
+// A node sorts n elements inside a region of n + b slots starting at slot r; s is
+// the input index of its first element.  side 0 = data-left (data ends in the
+// region's left n slots), side 1 = data-right.  Left children are data-left,
+// right children data-right, so the children's buffers meet in the middle of
+// the parent's region.  The odd surplus element goes to the outer child (left
+// child of a data-left node, right child of a data-right node); the root has
+// b = floor(n/2); the outer child gets floor(n_outer/2) buffer slots, the inner
+// child the rest -- never fewer than the inner child's element count, which is
+// what the in-place merge needs.
+//
+// Slots [0, n) are the caller's arrays, slots [n, n + floor(n/2)) the buffer.
+
+struct FrogNode {
+    int64_t n, b, r, s;
+    int32_t side, pad;
+};
+
+__device__ __forceinline__ void frog_split(const FrogNode& p, FrogNode& L, FrogNode& R)
+{
+    int64_t n_outer = (p.n + 1) / 2, n_inner = p.n - n_outer;
+    int64_t b_outer = n_outer / 2, b_inner = p.b - b_outer;
+    if (p.side == 0) { L.n = n_outer; L.b = b_outer; R.n = n_inner; R.b = b_inner; }
+    else             { L.n = n_inner; L.b = b_inner; R.n = n_outer; R.b = b_outer; }
+    L.side = 0; R.side = 1; L.pad = R.pad = 0;
+    L.r = p.r; R.r = p.r + L.n + L.b;
+    L.s = p.s; R.s = p.s + L.n;
+}
+
+__device__ __forceinline__ int64_t frog_data_slot(const FrogNode& x) { return x.side == 0 ? x.r : x.r + x.b; }
+
+struct Slots {
+    uint64_t* k0; uint32_t* v0;   // caller arrays: slots [0, n)
+    uint64_t* k1; uint32_t* v1;   // buffer: slots [n, n + b)
+    int64_t n;
+    __device__ __forceinline__ uint64_t* kp(int64_t s) const { return s < n ? k0 + s : k1 + (s - n); }
+    __device__ __forceinline__ uint32_t* vp(int64_t s) const { return s < n ? v0 + s : v1 + (s - n); }
+};
+
+// All nodes of depths 0..D in heap order: node k of depth d at (1 << d) - 1 + k.
+// Each thread walks from the root down the bits of k.
+__global__ void frog_plan_kernel(FrogNode* nodes, int64_t n, int D)
+{
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t total = (2ll << D) - 1;
+    if (idx >= total) return;
+    int d = 63 - __clzll(idx + 1);
+    int64_t k = idx + 1 - (1ll << d);
+    FrogNode x;
+    x.n = n; x.b = n / 2; x.r = 0; x.s = 0; x.side = 0; x.pad = 0;
+    for (int lvl = d - 1; lvl >= 0; --lvl) {
+        FrogNode L, R;
+        frog_split(x, L, R);
+        x = ((k >> lvl) & 1) ? R : L;
+    }
+    nodes[idx] = x;
+}
+
+// Largest leaf index j with leaves[j].s <= pos.
+__device__ __forceinline__ int64_t find_leaf(const FrogNode* leaves, int64_t nleaves, int64_t pos)
+{
+    int64_t lo = 0, hi = nleaves - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (leaves[mid].s <= pos) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Fused setup: every leaf's elements are read from the contiguous input, sorted
+// as a tile and written to the leaf's gapped data slots (Frogsort1 setup; the
+// destination is never left of the source).  A leaf's destination can overlap
+// the input of leaves to its right, so leaves are processed in descending order
+// by ticket, each publishes "inputs loaded" right after loading, and writes only
+// once every overlapped leaf has published.  Earlier tickets never wait on later
+// ones, so the waits cannot deadlock; they are bounded anyway.
+template <int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS)
+    frog_setup_kernel(Slots sl, const FrogNode* __restrict__ leaves, int64_t nleaves, int mode,
+                      int* ticket, int* loaded, int* call_err, uint64_t limit_ns,
+                      const int* presorted)
+{
+    constexpr int T = THREADS * ITEMS;
+    if (skip_all(presorted)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemKV<T>& sm = *reinterpret_cast<SmemKV<T>*>(smem_raw);
+    __shared__ int64_t s_leaf;
+    __shared__ int s_ok;
+    const int t = threadIdx.x;
+    if (t == 0) s_leaf = nleaves - 1 - atomicAdd(ticket, 1);
+    __syncthreads();
+    const int64_t leaf = s_leaf;
+    const FrogNode x = leaves[leaf];
+    const int nv = (int)x.n;
+#pragma unroll 4
+    for (int j = 0; j < ITEMS; ++j) {
+        int i = t + j * THREADS;
+        bool ok = i < nv;
+        int64_t g = x.s + i;
+        sm.k[pidx(i)] = ok ? encode_key(sl.k0[g], mode) : ~0ull;
+        sm.v[pidx(i)] = (ok && sl.v0) ? sl.v0[g] : 0u;
+    }
+    __syncthreads();
+    if (t == 0) st_release(&loaded[leaf], 1);
+    block_sort_smem<THREADS, ITEMS>(sm, nv);
+    const int64_t dslot = frog_data_slot(x);
+    if (t == 0) {
+        bool ok = true;
+        if (dslot < sl.n && nv > 0) {
+            int64_t j0 = find_leaf(leaves, nleaves, dslot);
+            int64_t j1 = find_leaf(leaves, nleaves, imin64(dslot + nv - 1, sl.n - 1));
+            for (int64_t j = imax64(j0, leaf + 1); j <= j1 && ok; ++j)
+                ok = wait_flag(&loaded[j], 1, call_err, limit_ns, GNS_ERR_TIMEOUT);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+#pragma unroll 4
+    for (int j = 0; j < ITEMS; ++j) {
+        int i = t + j * THREADS;
+        if (i < nv) {
+            *sl.kp(dslot + i) = sm.k[pidx(i)];
+            if (sl.v0) *sl.vp(dslot + i) = sm.v[pidx(i)];
+        }
+    }
+}
+
+// splits[k*nch + c] = co-rank (left-run elements) of output c*CHUNK of node k.
+__global__ void frog_partition_kernel(Slots sl, const FrogNode* __restrict__ level,
+                                      const FrogNode* __restrict__ child, int64_t nnodes, int64_t nch,
+                                      int64_t* splits, const int* presorted)
+{
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nnodes * nch || skip_all(presorted)) return;
+    int64_t k = idx / nch, c = idx % nch;
+    FrogNode x = level[k], L = child[2 * k], R = child[2 * k + 1];
+    int64_t diag = imin64(c * CHUNK, x.n);
+    int64_t ra = frog_data_slot(L), rb = frog_data_slot(R);
+    splits[idx] = merge_path(diag, L.n, R.n, [&](int64_t i) { return *sl.kp(ra + i); },
+                             [&](int64_t j) { return *sl.kp(rb + j); });
+}
+
+// One in-place symmetric merge level.  A data-left node writes its output to
+// slots [r, r+n); the only inputs it can overwrite are its left run's elements
+// (they move right), so its chunks run from the top down (descending tickets)
+// and chunk c writes after every later chunk that reads the left-run elements
+// under it has loaded.  A data-right node (output [r+b, r+b+n)) is the mirror
+// image: its right run's elements move left, chunks run bottom up.  The right
+// (left) run of a data-left (data-right) node is never overwritten, because the
+// node holds at least as many buffer slots as its inner child has elements.
+template <int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS)
+    frog_merge_kernel(Slots sl, const FrogNode* __restrict__ level, const FrogNode* __restrict__ child,
+                      int64_t nnodes, int64_t nch, const int64_t* __restrict__ splits, int mode,
+                      int decode_out, int* ticket, int* loaded, int* call_err, uint64_t limit_ns,
+                      int64_t skip_ticket, const int* presorted)
+{
+    constexpr int C = THREADS * ITEMS;
+    if (skip_all(presorted)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemKV<C>& sm = *reinterpret_cast<SmemKV<C>*>(smem_raw);
+    __shared__ int64_t s_tk;
+    __shared__ int s_ok;
+    const int t = threadIdx.x;
+    if (t == 0) s_tk = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int64_t tk = s_tk;
+    const int64_t k = tk / nch, local = tk % nch;
+    const FrogNode x = level[k];
+    const int64_t c = x.side == 0 ? nch - 1 - local : local;
+    const int64_t fi = k * nch + c;
+    const int64_t w0 = c * C;
+    if (w0 >= x.n) {
+        if (t == 0 && tk != skip_ticket) st_release(&loaded[fi], 1);
+        return;
+    }
+    const FrogNode L = child[2 * k], R = child[2 * k + 1];
+    const int64_t w1 = imin64(w0 + C, x.n);
+    const int64_t a0 = splits[fi];
+    const int64_t a1 = (w1 == x.n) ? L.n : splits[fi + 1];
+    const int na = (int)(a1 - a0), nb = (int)((w1 - a1) - (w0 - a0));
+    const int cnt = na + nb;
+    const int64_t ra = frog_data_slot(L) + a0, rb = frog_data_slot(R) + (w0 - a0);
+#pragma unroll 4
+    for (int j = 0; j < ITEMS; ++j) {
+        int i = t + j * THREADS;
+        if (i < cnt) {
+            int64_t s = i < na ? ra + i : rb + (i - na);
+            sm.k[pidx(i)] = *sl.kp(s);
+            sm.v[pidx(i)] = sl.v0 ? *sl.vp(s) : 0u;
+        }
+    }
+    __syncthreads();
+    if (t == 0 && tk != skip_ticket) st_release(&loaded[fi], 1);
+    uint64_t kk[ITEMS];
+    uint32_t vv[ITEMS];
+    const int diag = t * ITEMS;
+    if (diag < cnt) {
+        int ai = (int)merge_path(
+            diag, na, nb, [&](int64_t q) { return sm.k[pidx((int)q)]; },
+            [&](int64_t q) { return sm.k[pidx(na + (int)q)]; });
+        serial_merge<C, ITEMS>(sm, ai, na, na + diag - ai, cnt, cnt - 1, kk, vv);
+    }
+    __syncthreads();
+    if (diag < cnt) {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            if (diag + j < cnt) {
+                sm.k[pidx(diag + j)] = kk[j];
+                sm.v[pidx(diag + j)] = vv[j];
+            }
+        }
+    }
+    if (t == 0) {
+        bool ok = true;
+        const int64_t* sp = splits + k * nch;
+        if (x.side == 0) {
+            const int64_t lim = imin64(w1, L.n);   // left-run indices [w0, lim) are overwritten
+            if (w0 < lim)
+                for (int64_t c2 = c + 1; ok && c2 < nch && c2 * C < x.n && sp[c2] < lim; ++c2)
+                    ok = wait_flag(&loaded[k * nch + c2], 1, call_err, limit_ns, GNS_ERR_TIMEOUT);
+        } else {
+            const int64_t lo = imax64(w0 - L.n, 0);          // right-run indices [lo, hi)
+            const int64_t hi = imin64(w1 - L.n, R.n);
+            if (lo < hi)
+                for (int64_t c2 = c - 1; ok && c2 >= 0 && ((c2 + 1) * C - sp[c2 + 1]) > lo; --c2)
+                    ok = wait_flag(&loaded[k * nch + c2], 1, call_err, limit_ns, GNS_ERR_TIMEOUT);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const int64_t o = frog_data_slot(x) + w0;
+#pragma unroll 4
+    for (int j = 0; j < ITEMS; ++j) {
+        int i = t + j * THREADS;
+        if (i < cnt) {
+            uint64_t key = sm.k[pidx(i)];
+            *sl.kp(o + i) = decode_out ? decode_key(key, mode) : key;
+            if (sl.v0) *sl.vp(o + i) = sm.v[pidx(i)];
+        }
+    }
+}
+
+__global__ void publish_err_kernel(const int* call_err, int* status)
+{
+    int e = *call_err;
+    if (e != 0) atomicCAS(status, 0, e);
+}
+
+}  // namespace gns

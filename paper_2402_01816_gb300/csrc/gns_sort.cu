@@ -1,0 +1,220 @@
+// gns_sort.cu -- host orchestration of the plain stable mergesort (both tiers).
+//
+// Pass schedule for n > TILE:
+//   run detection (1 read pass; early exit for presorted / strictly reversed)
+//   100% tier : tile sort -> ceil(log2(n / TILE)) Nocopy merge levels, the tile
+//               sort writing to the buffer when the level count is odd so that
+//               the last level lands in the caller's arrays ("Forgotten art").
+//   50% tier  : node plan -> fused setup (tile sort + scatter into the gapped
+//               Frogsort1 leaf slots) -> one in-place merge level per tree depth
+//               ("Symmetric merging", "Frogsort1").
+// Keys are encoded (order map) when first read and decoded by the last write.
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <mutex>
+
+#include "gns_internal.h"
+#include "gns_kernels.cuh"
+
+namespace gns {
+
+namespace {
+
+constexpr size_t kSmemTile = sizeof(SmemKV<TILE>);
+constexpr size_t kSmemChunk = sizeof(SmemKV<CHUNK>);
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Merge levels of the 100% tier: ceil(log2(#tiles)).
+int merge_levels(int64_t n)
+{
+    int64_t tiles = ceil_div(n, TILE);
+    int L = 0;
+    while ((1ll << L) < tiles) ++L;
+    return L;
+}
+
+// Leaf depth of the Frogsort1 tree: the first depth whose nodes hold <= TILE
+// elements (node sizes at depth d are floor or ceil of n / 2^d).
+int frog_leaf_depth(int64_t n)
+{
+    int D = 0;
+    while (ceil_div(n, 1ll << D) > TILE) ++D;
+    return D;
+}
+
+int64_t frog_chunks(int64_t n, int d) { return ceil_div(ceil_div(n, 1ll << d), CHUNK); }
+
+struct Layout {
+    // control words (ints): [0..1] presorted flags, [2] call error
+    size_t ctl, bufk, bufv, splits, nodes, flags, tickets, total;
+    size_t flags_bytes, tickets_bytes;
+    int L, D;
+};
+
+Layout make_layout(int64_t n, double bf, bool with_vals)
+{
+    Layout o{};
+    size_t off = 0;
+    o.ctl = off; off += 256;
+    if (n <= TILE) { o.total = off; return o; }
+    if (bf >= 1.0) {
+        o.L = merge_levels(n);
+        int64_t nblocks = ceil_div(n, CHUNK);
+        o.bufk = off; off += align256((size_t)n * 8);
+        o.bufv = off; off += with_vals ? align256((size_t)n * 4) : 0;
+        o.splits = off; off += align256((size_t)nblocks * 8);
+    } else {
+        int D = frog_leaf_depth(n);
+        o.D = D;
+        int64_t b = n / 2;
+        o.bufk = off; off += align256((size_t)b * 8);
+        o.bufv = off; off += with_vals ? align256((size_t)b * 4) : 0;
+        o.nodes = off; off += align256((size_t)((2ll << D) - 1) * sizeof(FrogNode));
+        int64_t max_split = 0, nflags = 1ll << D;   // setup flags: one per leaf
+        for (int d = 0; d < D; ++d) {
+            int64_t e = (1ll << d) * frog_chunks(n, d);
+            if (e > max_split) max_split = e;
+            nflags += e;
+        }
+        o.splits = off; off += align256((size_t)max_split * 8);
+        o.flags = off; o.flags_bytes = align256((size_t)nflags * 4); off += o.flags_bytes;
+        o.tickets = off; o.tickets_bytes = align256((size_t)(D + 1) * 4); off += o.tickets_bytes;
+    }
+    o.total = off;
+    return o;
+}
+
+template <typename K>
+void set_smem(K kernel, size_t bytes)
+{
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+std::once_flag g_attr_once;
+
+void init_attributes()
+{
+    std::call_once(g_attr_once, [] {
+        set_smem(tile_sort_kernel<SORT_THREADS, SORT_ITEMS>, kSmemTile);
+        set_smem(merge_pass_kernel<MERGE_THREADS, MERGE_ITEMS>, kSmemChunk);
+        set_smem(frog_setup_kernel<SORT_THREADS, SORT_ITEMS>, kSmemTile);
+        set_smem(frog_merge_kernel<MERGE_THREADS, MERGE_ITEMS>, kSmemChunk);
+    });
+}
+
+#define GNS_TRY(x)                              \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) {                \
+            rc = GNS_ERR_CUDA;                  \
+            goto done;                          \
+        }                                       \
+    } while (0)
+
+}  // namespace
+
+cudaError_t publish_call_error(const int* call_err, cudaStream_t s)
+{
+    int* st = status_word_ptr();
+    if (!st) return cudaErrorUnknown;
+    return launch(K_ERR_PUBLISH, publish_err_kernel, dim3(1), dim3(1), 0, s, call_err, st);
+}
+
+size_t sort_workspace_bytes(int64_t n, double bf)
+{
+    if (n <= 1) return 0;
+    return make_layout(n, bf, true).total;
+}
+
+int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, cudaStream_t s)
+{
+    if (n <= 1) return GNS_OK;
+    const Layout lay = make_layout(n, bf, vals != nullptr);
+    char* ws = (char*)ws_alloc(lay.total, s);
+    if (!ws) return GNS_ERR_OOM;
+    init_attributes();
+    int rc = GNS_OK;
+    int* ctl = (int*)(ws + lay.ctl);
+    int* presorted = ctl;
+    int* call_err = ctl + 2;
+    const int* skip = presorted;
+
+    GNS_TRY(cudaMemsetAsync(ctl, 0, 256, s));
+    GNS_TRY(cudaMemsetAsync(presorted, 1, 2 * sizeof(int), s));   // both flags "true"
+    GNS_TRY(launch(K_RUN_DETECT, run_detect_kernel, dim3((unsigned)ceil_div(n, DETECT_TILE)), dim3(256), 0, s,
+                   (const uint64_t*)keys, n, mode, presorted));
+    GNS_TRY(launch(K_REVERSE, reverse_kernel, dim3(152 * 8), dim3(256), 0, s, keys, vals, n, (const int*)presorted));
+
+    if (n <= TILE) {
+        GNS_TRY(launch(K_TILE_SORT, tile_sort_kernel<SORT_THREADS, SORT_ITEMS>, dim3(1), dim3(SORT_THREADS),
+                       kSmemTile, s, (const uint64_t*)keys, (const uint32_t*)vals, keys, vals, n, mode, 1, skip));
+    } else if (bf >= 1.0) {
+        const int L = lay.L;
+        uint64_t* bufk = (uint64_t*)(ws + lay.bufk);
+        uint32_t* bufv = vals ? (uint32_t*)(ws + lay.bufv) : nullptr;
+        int64_t* splits = (int64_t*)(ws + lay.splits);
+        uint64_t* cur_k = (L & 1) ? bufk : keys;
+        uint32_t* cur_v = (L & 1) ? bufv : vals;
+        uint64_t* oth_k = (L & 1) ? keys : bufk;
+        uint32_t* oth_v = (L & 1) ? vals : bufv;
+        const int64_t tiles = ceil_div(n, TILE);
+        GNS_TRY(launch(K_TILE_SORT, tile_sort_kernel<SORT_THREADS, SORT_ITEMS>, dim3((unsigned)tiles),
+                       dim3(SORT_THREADS), kSmemTile, s, (const uint64_t*)keys, (const uint32_t*)vals, cur_k,
+                       cur_v, n, mode, 0, skip));
+        const int64_t nblocks = ceil_div(n, CHUNK);
+        for (int lvl = 0; lvl < L; ++lvl) {
+            const int64_t w = (int64_t)TILE << lvl;
+            GNS_TRY(launch(K_MERGE_PARTITION, merge_partition_kernel, dim3((unsigned)ceil_div(nblocks, 256)),
+                           dim3(256), 0, s, (const uint64_t*)cur_k, n, w, nblocks, splits, skip));
+            GNS_TRY(launch(K_MERGE_PASS, merge_pass_kernel<MERGE_THREADS, MERGE_ITEMS>, dim3((unsigned)nblocks),
+                           dim3(MERGE_THREADS), kSmemChunk, s, (const uint64_t*)cur_k, (const uint32_t*)cur_v,
+                           oth_k, oth_v, n, w, (const int64_t*)splits, mode, (int)(lvl == L - 1), skip));
+            uint64_t* tk = cur_k; cur_k = oth_k; oth_k = tk;
+            uint32_t* tv = cur_v; cur_v = oth_v; oth_v = tv;
+        }
+    } else {
+        const int D = lay.D;
+        Slots sl;
+        sl.k0 = keys; sl.v0 = vals; sl.n = n;
+        sl.k1 = (uint64_t*)(ws + lay.bufk);
+        sl.v1 = vals ? (uint32_t*)(ws + lay.bufv) : nullptr;
+        FrogNode* nodes = (FrogNode*)(ws + lay.nodes);
+        int64_t* splits = (int64_t*)(ws + lay.splits);
+        int* flags = (int*)(ws + lay.flags);
+        int* tickets = (int*)(ws + lay.tickets);
+        const uint64_t limit = wait_limit_ns();
+        GNS_TRY(cudaMemsetAsync(flags, 0, lay.flags_bytes + lay.tickets_bytes, s));
+        const int64_t total_nodes = (2ll << D) - 1;
+        GNS_TRY(launch(K_FROG_PLAN, frog_plan_kernel, dim3((unsigned)ceil_div(total_nodes, 256)), dim3(256), 0, s,
+                       nodes, n, D));
+        const int64_t nleaves = 1ll << D;
+        const FrogNode* leaves = nodes + (nleaves - 1);
+        GNS_TRY(launch(K_FROG_SETUP, frog_setup_kernel<SORT_THREADS, SORT_ITEMS>, dim3((unsigned)nleaves),
+                       dim3(SORT_THREADS), kSmemTile, s, sl, leaves, nleaves, mode, tickets + D, flags, call_err,
+                       limit, skip));
+        int* lflags = flags + nleaves;
+        int64_t skip_ticket = take_debug_skip_publish();
+        for (int d = D - 1; d >= 0; --d) {
+            const int64_t nnodes = 1ll << d;
+            const int64_t nch = frog_chunks(n, d);
+            const FrogNode* level = nodes + (nnodes - 1);
+            const FrogNode* child = nodes + (2 * nnodes - 1);
+            GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel, dim3((unsigned)ceil_div(nnodes * nch, 256)),
+                           dim3(256), 0, s, sl, level, child, nnodes, nch, splits, skip));
+            GNS_TRY(launch(K_FROG_MERGE, frog_merge_kernel<MERGE_THREADS, MERGE_ITEMS>,
+                           dim3((unsigned)(nnodes * nch)), dim3(MERGE_THREADS), kSmemChunk, s, sl, level, child,
+                           nnodes, nch, (const int64_t*)splits, mode, (int)(d == 0), tickets + d, lflags, call_err,
+                           limit, skip_ticket, skip));
+            skip_ticket = -1;
+            lflags += nnodes * nch;
+        }
+    }
+    GNS_TRY(publish_call_error(call_err, s));
+done:
+    ws_free(ws, s);
+    return rc;
+}
+
+}  // namespace gns

@@ -1,0 +1,102 @@
+"""The C-ABI library loads, exports every symbol include/gns.h declares, and
+rejects bad arguments on the host before any device work (CPU only)."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2402_01816_gb300 import build
+    build.build()
+    from paper_2402_01816_gb300 import _native
+    return _native.lib()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            src = re.sub(r"//[^\n]*", "", src)
+            names |= set(re.findall(r"\b(gns_[a-z0-9_]+)\s*\(", src))
+    return names - {"gns_alloc_fn", "gns_free_fn"}
+
+
+def test_exports_every_declared_symbol(L):
+    declared = _declared()
+    assert len(declared) >= 15
+    for name in sorted(declared):
+        assert hasattr(L, name), f"{name} declared in include/ but not exported"
+
+
+def test_strerror_and_version(L):
+    from paper_2402_01816_gb300 import _native
+    for code in (0, -1, -2, -3, -4, -5):
+        assert L.gns_strerror(code)
+    assert b"sm_103a" in L.gns_version()
+    assert _native.strerror(-5) == "device-side wait timed out"
+
+
+FAKE = 1 << 40   # a device-looking address; validation fails before any use
+
+
+@pytest.mark.parametrize("args,code", [
+    ((FAKE, None, -1, 0, 1.0), -1),            # n < 0
+    ((None, None, 10, 0, 1.0), -1),            # NULL keys with n > 0
+    ((FAKE, None, 10, 2, 1.0), -1),            # unknown order
+    ((FAKE, None, 10, 0, math.nan), -1),       # NaN buffer fraction
+    ((FAKE, None, 10, 0, -0.5), -1),           # negative buffer fraction
+    ((FAKE, None, 10, 0, 0.3), -2),            # below the 50% tier
+    ((FAKE + 4, None, 10, 0, 1.0), -1),        # keys not 8-byte aligned
+    ((FAKE, FAKE + 2, 10, 0, 1.0), -1),        # payload misaligned
+    ((FAKE, FAKE + 40, 10, 0, 1.0), -1),       # keys and payload overlap
+    ((None, None, 0, 0, 1.0), 0),              # n == 0 is a no-op
+    ((FAKE, None, 1, 0, 0.5), 0),              # n == 1 is a no-op
+])
+def test_host_argument_checks(L, args, code):
+    k, p, n, order, bf = args
+    for fn in (L.gns_sort, L.gns_sort_i64):
+        assert fn(k, p, n, order, bf, None) == code
+
+
+def test_allocator_failure_is_oom(L):
+    ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+    FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+    calls = []
+
+    @ALLOC
+    def fail_alloc(nbytes, stream, ctx):
+        calls.append(nbytes)
+        return None
+
+    @FREE
+    def no_free(p, stream, ctx):
+        raise AssertionError("free of a failed allocation")
+
+    L.gns_set_allocator(ctypes.cast(fail_alloc, ctypes.c_void_p), ctypes.cast(no_free, ctypes.c_void_p), None)
+    try:
+        assert L.gns_sort(FAKE, FAKE + (1 << 30), 1 << 20, 0, 1.0, None) == -3
+        assert L.gns_sort(FAKE, None, 1 << 20, 1, 0.5, None) == -3
+        assert len(calls) == 2 and calls[0] >= 12 * (1 << 20)
+    finally:
+        L.gns_set_allocator(None, None, None)
+
+
+def test_workspace_bytes_match_tiers(L):
+    n = 1 << 27
+    full = L.gns_workspace_bytes(n, 1.0, 0)
+    half = L.gns_workspace_bytes(n, 0.5, 0)
+    # %RAM = (12 n + workspace) / 12 n  (Sustainability measures section)
+    ram_full = (12 * n + full) / (12 * n)
+    ram_half = (12 * n + half) / (12 * n)
+    assert 2.0 <= ram_full < 2.01
+    assert 1.5 <= ram_half < 1.51
+    assert L.gns_workspace_bytes(1, 1.0, 0) == 0
+    assert L.gns_workspace_bytes(4096, 1.0, 0) <= 4096

@@ -1,0 +1,66 @@
+"""Full-size checks at the benchmark's workload (2^27 float64 keys + uint32
+index payload, four patterns, both tiers), in the benchmark's launch
+configuration: invariants that hold at any size plus sampled output positions
+computed one by one by the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2402_01816_gb300 import inputs
+from tests.gpu_util import need_gpu, to_dev_keys, to_dev_payload, torch
+
+pytestmark = pytest.mark.gpu
+
+N_FULL = 1 << 27
+
+
+def check_sorted_stable(keys_in, k_out, p_out, order=0, samples=12, seed=0):
+    n = keys_in.size
+    # a permutation carried by the payload, moving the original bit patterns
+    assert np.array_equal(np.sort(p_out), np.arange(n, dtype=np.uint32))
+    assert np.array_equal(k_out.view(np.uint64), keys_in.view(np.uint64)[p_out])
+    # finite keys without -0.0: order by float comparison; ties in input order
+    d = np.diff(k_out)
+    if order == 0:
+        assert np.all(d >= 0)
+    else:
+        assert np.all(d <= 0)
+    eq = d == 0
+    assert np.all(p_out[1:][eq] > p_out[:-1][eq])
+    # sampled final positions from the oracle (rank counting, one by one)
+    rng = np.random.default_rng(seed)
+    for i in rng.integers(0, n, samples):
+        pos = oracle.final_position(keys_in, int(i), oracle.DESC if order else oracle.ASC)
+        assert p_out[pos] == i
+
+
+@pytest.mark.parametrize("bf", [1.0, 0.5])
+@pytest.mark.parametrize("pattern", inputs.PATTERNS_C1)
+def test_config_full_size(pattern, bf):
+    need_gpu()
+    import paper_2402_01816_gb300 as g
+    keys = inputs.make_keys(pattern, N_FULL, seed=0)
+    kt = to_dev_keys(keys)
+    pt = to_dev_payload(inputs.index_payload(N_FULL))
+    g.gns_sort(kt, pt, buffer_fraction=bf)
+    assert g.gns_stream_status() == 0
+    k_out = kt.cpu().numpy()
+    p_out = pt.cpu().numpy().view(np.uint32)
+    del kt, pt
+    torch.cuda.empty_cache()
+    check_sorted_stable(keys, k_out, p_out)
+
+
+def test_small_config_exact():
+    """2^20 uniform[0,1) keys, ascending, 100% buffer: bit-exact against the
+    oracle's full stable sort."""
+    need_gpu()
+    import paper_2402_01816_gb300 as g
+    n = 1 << 20
+    keys = inputs.make_keys("uniform", n, seed=0)
+    pay = inputs.index_payload(n)
+    kt, pt = to_dev_keys(keys), to_dev_payload(pay)
+    g.gns_sort(kt, pt, buffer_fraction=1.0)
+    want_k, want_p = oracle.stable_sort(keys, pay)
+    assert np.array_equal(kt.cpu().numpy().view(np.uint64), want_k.view(np.uint64))
+    assert np.array_equal(pt.cpu().numpy().view(np.uint32), want_p)

@@ -1,0 +1,138 @@
+"""Parity of gns_sort (both memory tiers) with the oracle's definition of the
+stable sort, element by element and bit-exact (keys and payload)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2402_01816_gb300 import inputs
+from tests.gpu_util import assert_bitexact, from_dev, need_gpu, to_dev_keys, to_dev_payload, torch
+
+pytestmark = pytest.mark.gpu
+
+TILE = 4096
+SIZES = [0, 1, 2, 3, 17, 255, TILE - 1, TILE, TILE + 1, 2 * TILE - 1, 2 * TILE + 1, 3 * TILE + 5,
+         5 * TILE, 7 * TILE + 3, 16 * TILE, 16 * TILE + 1, 33 * TILE + 77, (1 << 18) + 12345]
+TIERS = [1.0, 0.5]
+
+
+def _run(keys, order, bf, with_payload=True):
+    import paper_2402_01816_gb300 as g
+    n = keys.size
+    pay = inputs.index_payload(n)
+    kt = to_dev_keys(keys)
+    pt = to_dev_payload(pay) if with_payload else None
+    g.gns_sort(kt, pt, order=order, buffer_fraction=bf)
+    assert g.gns_stream_status() == 0
+    got_k, got_p = from_dev(kt, pt)
+    want_k, want_p = oracle.stable_sort(keys, pay if with_payload else None,
+                                        oracle.DESC if order == 1 else oracle.ASC)
+    assert_bitexact(got_k, got_p, want_k, want_p)
+
+
+@pytest.mark.parametrize("bf", TIERS)
+@pytest.mark.parametrize("n", SIZES)
+def test_uniform_sizes(n, bf):
+    need_gpu()
+    _run(inputs.make_keys("uniform", n, seed=n), 0, bf)
+
+
+@pytest.mark.parametrize("bf", TIERS)
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("pattern", ["permut", "ties", "asc_noise", "desc", "tielog2", "asclocal",
+                                     "ascglobal", "desclocal", "descglobal", "ascall", "descall",
+                                     "presorted_runs", "mixture"])
+def test_patterns(pattern, order, bf):
+    need_gpu()
+    n = 70 * TILE + 1234
+    _run(inputs.make_keys(pattern, n, seed=3), order, bf)
+
+
+@pytest.mark.parametrize("bf", TIERS)
+@pytest.mark.parametrize("order", [0, 1])
+def test_edge_keys_and_int64(order, bf):
+    need_gpu()
+    rng = np.random.default_rng(7)
+    alpha = inputs.edge_alphabet()
+    for n in (5, TILE + 3, 9 * TILE + 1):
+        _run(alpha[rng.integers(0, alpha.size, n)], order, bf)
+        _run(rng.integers(-2**63, 2**63 - 1, n, dtype=np.int64, endpoint=True), order, bf)
+        _run(rng.integers(-3, 3, n).astype(np.int64), order, bf)
+
+
+@pytest.mark.parametrize("bf", TIERS)
+def test_all_equal_and_two_values(bf):
+    need_gpu()
+    for n in (TILE * 3 + 7, 100000):
+        _run(np.full(n, 2.5), 0, bf)
+        _run(np.full(n, 2.5), 1, bf)
+        k = np.where(np.arange(n) % 3 == 0, 1.0, -1.0)
+        _run(k, 0, bf)
+
+
+@pytest.mark.parametrize("bf", TIERS)
+def test_keys_only(bf):
+    need_gpu()
+    for n in (3, TILE + 1, 20 * TILE + 9):
+        _run(inputs.make_keys("ties", n, seed=1), 0, bf, with_payload=False)
+
+
+@pytest.mark.parametrize("bf", TIERS)
+def test_offset_views(bf):
+    """Tensors that are views at odd element offsets into a larger allocation."""
+    need_gpu()
+    import paper_2402_01816_gb300 as g
+    n = 12 * TILE + 5
+    keys = inputs.make_keys("uniform", n, seed=9)
+    pay = inputs.index_payload(n)
+    big_k = torch.zeros(n + 3, dtype=torch.float64, device="cuda")
+    big_p = torch.zeros(n + 5, dtype=torch.int32, device="cuda")
+    kt, pt = big_k[3:], big_p[1:n + 1]
+    kt.copy_(torch.from_numpy(keys))
+    pt.copy_(torch.from_numpy(pay.view(np.int32)))
+    g.gns_sort(kt, pt, buffer_fraction=bf)
+    want_k, want_p = oracle.stable_sort(keys, pay)
+    got_k, got_p = from_dev(kt, pt)
+    assert_bitexact(got_k, got_p, want_k, want_p)
+    assert big_k[:3].abs().sum().item() == 0 and big_p[0].item() == 0 and big_p[n + 1:].abs().sum().item() == 0
+
+
+def test_host_entry_point():
+    need_gpu()
+    import paper_2402_01816_gb300 as g
+    for bf in TIERS:
+        for n in (1000, 9 * TILE + 2):
+            keys = inputs.make_keys("ties", n, seed=4)
+            pay = inputs.index_payload(n)
+            k, p = keys.copy(), pay.copy()
+            g.gns_sort_host(k, p, buffer_fraction=bf)
+            want_k, want_p = oracle.stable_sort(keys, pay)
+            assert_bitexact(k, p, want_k, want_p)
+
+
+def test_bounded_wait_timeout_then_recovery():
+    """A CTA of the in-place tier skips publishing its "inputs loaded" flag: the
+    CTA that depends on it gives up after the wait limit, the call reports
+    GNS_ERR_TIMEOUT through the status word, and the next call is correct."""
+    need_gpu()
+    import paper_2402_01816_gb300 as g
+    n = 1 << 16
+    keys = inputs.make_keys("uniform", n, seed=12)
+    kt = to_dev_keys(keys)
+    g.gns_set_wait_limit_ns(20_000_000)
+    try:
+        g.gns_debug_skip_publish(0)
+        g.gns_sort(kt, None, buffer_fraction=0.5)
+        assert g.gns_stream_status() == g.GNS_ERR_TIMEOUT
+        assert g.gns_stream_status() == 0       # cleared by the read
+    finally:
+        g.gns_debug_skip_publish(-1)
+        g.gns_set_wait_limit_ns(2_000_000_000)
+    _run(keys, 0, 0.5)
+
+
+def test_workspace_matches_tier_ram():
+    need_gpu()
+    import paper_2402_01816_gb300 as g
+    n = 1 << 22
+    assert g.gns_workspace_bytes(n, 1.0) >= 12 * n
+    assert 6 * n <= g.gns_workspace_bytes(n, 0.5) < 6.1 * n
