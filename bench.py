@@ -245,12 +245,15 @@ def run_ours(args, ws, rank, local):
             kt.copy_(pristine[p])
             pt.copy_(pay_pristine)
 
-    def one_step(evs=None):
+    def one_step(evs=None, owners=None):
         for i, c in enumerate(combos):
             kt, pt = work[c]
             if evs is not None:
                 evs[i][0].record(stream)
+            l0 = g.gns_launch_count()
             g.gns_sort(kt, pt, order=0, buffer_fraction=c[1], stream=stream)
+            if owners is not None:
+                owners.extend([c] * (g.gns_launch_count() - l0))
             if evs is not None:
                 evs[i][1].record(stream)
 
@@ -263,7 +266,7 @@ def run_ours(args, ws, rank, local):
 
     step_ms, per_combo = [], {c: [] for c in combos}
     launches0 = g.gns_launch_count()
-    prof = []
+    prof = []          # (combo, kernel name, ms) of every launch in the timed region
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             restore()
@@ -273,8 +276,9 @@ def run_ours(args, ws, rank, local):
             g.gns_profile_enable(True)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in combos]
+            owners = []
             e0.record(stream)
-            one_step(evs)
+            one_step(evs, owners)
             e1.record(stream)
             torch.cuda.synchronize()
             g.gns_profile_enable(False)
@@ -282,7 +286,9 @@ def run_ours(args, ws, rank, local):
             step_ms.append(e0.elapsed_time(e1))
             for c, (a, b) in zip(combos, evs):
                 per_combo[c].append(a.elapsed_time(b))
-            prof.extend(g.gns_profile_read())
+            recs = g.gns_profile_read()
+            assert len(recs) == len(owners), (len(recs), len(owners))
+            prof.extend((c, name, t) for c, (name, t) in zip(owners, recs))
     launches = g.gns_launch_count() - launches0
     status = g.gns_stream_status()
     if status != 0:
@@ -298,34 +304,37 @@ def run_ours(args, ws, rank, local):
     keys_per_step = n * len(combos) * ws
     value = keys_per_step / (ms / 1e3) / 1e9
 
-    # roofline of the dominant kernel (the 100% tier merge pass) and the others
+    # Roofline of the dominant kernel: the 100% tier merge pass, over the sorts
+    # that run merge levels (the strictly descending pattern is reversed once and
+    # its merge launches return at once, so they are left out of the average).
     peak, peak_kind = load_peaks()
-    by_kernel = {}
-    for name, t in prof:
-        by_kernel.setdefault(name, []).append(t)
-    total_kernel_ms = sum(sum(v) for v in by_kernel.values())
+    moving = [c for c in combos if c[0] != "desc"]
+    total_kernel_ms = sum(t for _, _, t in prof)
 
-    def roof(name):
-        if name not in by_kernel:
+    def roof(name, among):
+        ts = [t for c, nm, t in prof if nm == name and c in among]
+        if not ts:
             return None
-        avg = statistics.mean(by_kernel[name])
+        avg = statistics.mean(ts)
         alg = BYTES_PER_ELEM_PASS * n
         ach = alg / (avg / 1e3) / 1e9
-        return {"launches": len(by_kernel[name]), "avg_ms": avg, "algorithmic_bytes_per_launch": alg,
+        return {"launches": len(ts), "avg_ms": avg, "algorithmic_bytes_per_launch": alg,
                 "achieved_gbs": ach, "frac": ach / peak,
-                "share": sum(by_kernel[name]) / total_kernel_ms if total_kernel_ms else None}
+                "share": sum(t for c, nm, t in prof if nm == name) / total_kernel_ms}
 
-    mp = roof("merge_pass")
+    mp = roof("merge_pass", moving)
     roofline = {"bound": "hbm", "achieved": mp["achieved_gbs"] if mp else None, "peak": peak, "unit": "GB/s",
                 "frac": mp["frac"] if mp else None, "traffic": ncu_traffic("merge_pass"),
-                "kernel": "merge_pass (100% tier, one merge level over all n)",
-                "peak_source": f"{peak_kind} HBM copy bandwidth", "note": "frac is of measured peak"
-                if peak_kind == "measured" else "frac is of fallback peak"}
+                "kernel": "merge_pass (100% tier merge level over all n; 24 B per element)",
+                "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6800 GB/s",
+                "note": "frac of measured peak" if peak_kind == "measured" else "frac of fallback peak"}
     kernels = {}
-    for name in sorted(by_kernel):
-        r = roof(name) if name in ("merge_pass", "frog_merge", "tile_sort", "frog_setup") else None
-        kernels[name] = r or {"launches": len(by_kernel[name]), "avg_ms": statistics.mean(by_kernel[name]),
-                              "share": sum(by_kernel[name]) / total_kernel_ms if total_kernel_ms else None}
+    for name in sorted({nm for _, nm, _ in prof}):
+        ts = [t for _, nm, t in prof if nm == name]
+        r = roof(name, moving) if name in ("merge_pass", "frog_merge", "tile_sort", "frog_setup") else None
+        kernels[name] = r or {"launches": len(ts), "avg_ms": statistics.mean(ts),
+                              "share": sum(ts) / total_kernel_ms}
 
     detail = {}
     for c in combos:

@@ -147,6 +147,12 @@ typedef void* (*gns_alloc_fn)(size_t bytes, gns_stream_t stream, void* ctx);
 typedef void (*gns_free_fn)(void* ptr, gns_stream_t stream, void* ctx);
 void gns_set_allocator(gns_alloc_fn alloc, gns_free_fn free_fn, void* ctx);
 
+/* The default allocator keeps freed workspace in a per-device memory pool for
+ * the next call (no unmapping between calls).  This synchronises the current
+ * device and returns that cached memory to the driver.  Returns GNS_OK or
+ * GNS_ERR_CUDA. */
+int gns_release_workspace_cache(void);
+
 /* Synchronises `stream`, returns the current device's status word (GNS_OK or
  * the first device-side error since the last read) and clears it. */
 int gns_stream_status(gns_stream_t stream);

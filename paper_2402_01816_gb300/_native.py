@@ -51,6 +51,7 @@ def lib() -> ctypes.CDLL:
                 "gns_workspace_bytes": ([i64, f64, i32], ctypes.c_size_t),
                 "gns_set_allocator": ([P, P, P], None),
                 "gns_stream_status": ([P], i32),
+                "gns_release_workspace_cache": ([], i32),
                 "gns_strerror": ([i32], ctypes.c_char_p),
                 "gns_version": ([], ctypes.c_char_p),
                 "gns_launch_count": ([], u64),
@@ -159,6 +160,10 @@ def gns_workspace_bytes(n: int, buffer_fraction: float = 1.0, kind: int = WS_SOR
 
 def gns_stream_status(stream=None) -> int:
     return int(lib().gns_stream_status(_stream(stream)))
+
+
+def gns_release_workspace_cache() -> None:
+    _check(lib().gns_release_workspace_cache(), "gns_release_workspace_cache")
 
 
 def gns_version() -> str:

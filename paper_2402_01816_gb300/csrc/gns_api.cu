@@ -56,12 +56,50 @@ gns_free_fn g_free = nullptr;
 void* g_alloc_ctx = nullptr;
 }
 
+// The default allocator is a dedicated stream-ordered memory pool per device
+// whose release threshold is "never": freed workspace stays mapped for the next
+// call instead of being unmapped at every synchronisation.
+namespace {
+std::mutex g_pool_mu;
+std::vector<cudaMemPool_t> g_pools;   // indexed by device ordinal
+}
+
+cudaMemPool_t workspace_pool(int dev)
+{
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if ((int)g_pools.size() <= dev) g_pools.resize(dev + 1, nullptr);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pools[dev] = pool;
+    }
+    return g_pools[dev];
+}
+
 void* ws_alloc(size_t bytes, cudaStream_t s)
 {
     if (bytes == 0) bytes = 256;
     if (g_alloc) return g_alloc(bytes, (gns_stream_t)s, g_alloc_ctx);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaMemPool_t pool = workspace_pool(dev);
+    if (!pool) return nullptr;
     void* p = nullptr;
-    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync(&p, bytes, pool, s) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
@@ -299,6 +337,16 @@ const char* gns_kernel_name(int kernel_id)
 {
     if (kernel_id < 0 || kernel_id >= K_COUNT) return "unknown";
     return kernel_names[kernel_id];
+}
+
+int gns_release_workspace_cache(void)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GNS_ERR_CUDA;
+    cudaMemPool_t pool = workspace_pool(dev);
+    if (!pool) return GNS_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return GNS_ERR_CUDA;
+    return cudaMemPoolTrimTo(pool, 0) == cudaSuccess ? GNS_OK : GNS_ERR_CUDA;
 }
 
 void gns_set_wait_limit_ns(uint64_t ns) { g_wait_limit_ns.store(ns ? ns : 1); }

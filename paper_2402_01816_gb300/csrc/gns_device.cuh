@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/gns.h"
+
 namespace gns {
 
 constexpr uint64_t kSignBit = 0x8000000000000000ull;

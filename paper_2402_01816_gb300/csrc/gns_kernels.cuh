@@ -28,9 +28,7 @@ namespace gns {
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_ITEMS = 16;
 constexpr int TILE = SORT_THREADS * SORT_ITEMS;       // 4096 elements
-constexpr int MERGE_THREADS = 256;
-constexpr int MERGE_ITEMS = 16;
-constexpr int CHUNK = MERGE_THREADS * MERGE_ITEMS;    // 4096 outputs per CTA
+constexpr int CHUNK = 1024;                           // outputs per merge chunk
 constexpr int DETECT_TILE = 4096;
 
 // Shared-memory index with one pad slot per 16 elements: thread t's blocked
@@ -141,26 +139,40 @@ __device__ void block_sort_smem(SmemKV<THREADS * ITEMS>& sm, int n_valid)
 
 // presorted[0]: every adjacent pair non-decreasing (under the call's order);
 // presorted[1]: every adjacent pair strictly decreasing.  Both start at 1; any
-// CTA finding a violation clears the flag.  CTAs that start after both flags are
-// cleared return without reading (random inputs cost about one wave).
+// CTA finding a violation clears the flag.  Persistent CTAs walk tiles of
+// DETECT_TILE keys (one coalesced load per key, staged in shared memory with the
+// key before the tile) and stop as soon as both flags are cleared, so random
+// inputs cost about one wave.
 __global__ void __launch_bounds__(256) run_detect_kernel(const uint64_t* __restrict__ keys, int64_t n,
                                                          int mode, int* presorted)
 {
-    if (ld_relaxed(&presorted[0]) == 0 && ld_relaxed(&presorted[1]) == 0) return;
-    const int64_t base = (int64_t)blockIdx.x * DETECT_TILE;
-    const int64_t end = imin64(base + DETECT_TILE, n);
-    bool asc = true, desc = true;
-    for (int64_t i = base + threadIdx.x; i < end; i += blockDim.x) {
-        if (i == 0) continue;
-        uint64_t x = encode_key(keys[i - 1], mode), y = encode_key(keys[i], mode);
-        asc &= (x <= y);
-        desc &= (x > y);
-    }
-    asc = __syncthreads_and(asc);
-    desc = __syncthreads_and(desc);
-    if (threadIdx.x == 0) {
-        if (!asc) atomicAnd(&presorted[0], 0);
-        if (!desc) atomicAnd(&presorted[1], 0);
+    __shared__ uint64_t sk[DETECT_TILE + 1];
+    __shared__ int s_go;
+    const int t = threadIdx.x;
+    for (int64_t tile = blockIdx.x; tile * DETECT_TILE < n; tile += gridDim.x) {
+        if (t == 0) s_go = (ld_relaxed(&presorted[0]) | ld_relaxed(&presorted[1])) != 0;
+        __syncthreads();
+        if (!s_go) return;
+        const int64_t base = tile * DETECT_TILE;
+        const int cnt = (int)imin64(DETECT_TILE, n - base);     // pairs (g-1, g) for g in [base, base+cnt)
+        for (int i = t; i <= cnt; i += blockDim.x) {
+            int64_t g = base - 1 + i;
+            sk[i] = g >= 0 ? encode_key(keys[g], mode) : 0;
+        }
+        __syncthreads();
+        bool asc = true, desc = true;
+        for (int i = t; i < cnt; i += blockDim.x) {
+            if (base + i == 0) continue;
+            uint64_t x = sk[i], y = sk[i + 1];
+            asc &= (x <= y);
+            desc &= (x > y);
+        }
+        asc = __syncthreads_and(asc);
+        desc = __syncthreads_and(desc);
+        if (t == 0) {
+            if (!asc) atomicAnd(&presorted[0], 0);
+            if (!desc) atomicAnd(&presorted[1], 0);
+        }
     }
 }
 
@@ -240,77 +252,6 @@ __global__ void merge_partition_kernel(const uint64_t* __restrict__ k, int64_t n
     const uint64_t* B = k + ps + lenA;
     splits[b] = merge_path(out0 - ps, lenA, lenB, [&](int64_t x) { return A[x]; },
                            [&](int64_t x) { return B[x]; });
-}
-
-// One Nocopy merge level: runs of width w in src merged pairwise into dst.
-template <int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS)
-    merge_pass_kernel(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sv,
-                      uint64_t* __restrict__ dk, uint32_t* __restrict__ dv, int64_t n, int64_t w,
-                      const int64_t* __restrict__ splits, int mode, int decode_out,
-                      const int* presorted)
-{
-    constexpr int C = THREADS * ITEMS;
-    if (skip_all(presorted)) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SmemKV<C>& sm = *reinterpret_cast<SmemKV<C>*>(smem_raw);
-    const int t = threadIdx.x;
-    const int64_t b = blockIdx.x;
-    const int64_t out0 = b * C;
-    const int64_t ps = (out0 / (2 * w)) * (2 * w);
-    const int64_t lenA = imin64(w, n - ps);
-    const int64_t lenB = imax64(0, imin64(w, n - ps - w));
-    const int64_t tot = lenA + lenB;
-    const int64_t d0 = out0 - ps, d1 = imin64(d0 + C, tot);
-    const int64_t a0 = splits[b];
-    const int64_t a1 = (d1 == tot) ? lenA : splits[b + 1];
-    const int na = (int)(a1 - a0), nb = (int)((d1 - a1) - (d0 - a0));
-    const int cnt = na + nb;
-    const uint64_t* A = sk + ps + a0;
-    const uint64_t* B = sk + ps + lenA + (d0 - a0);
-    const uint32_t* Av = sv ? sv + ps + a0 : nullptr;
-    const uint32_t* Bv = sv ? sv + ps + lenA + (d0 - a0) : nullptr;
-#pragma unroll 4
-    for (int j = 0; j < ITEMS; ++j) {
-        int i = t + j * THREADS;
-        if (i < cnt) {
-            bool fa = i < na;
-            sm.k[pidx(i)] = fa ? A[i] : B[i - na];
-            sm.v[pidx(i)] = sv ? (fa ? Av[i] : Bv[i - na]) : 0u;
-        }
-    }
-    __syncthreads();
-    uint64_t k[ITEMS];
-    uint32_t v[ITEMS];
-    const int diag = t * ITEMS;
-    if (diag < cnt) {
-        int ai = (int)merge_path(
-            diag, na, nb, [&](int64_t x) { return sm.k[pidx((int)x)]; },
-            [&](int64_t x) { return sm.k[pidx(na + (int)x)]; });
-        serial_merge<C, ITEMS>(sm, ai, na, na + diag - ai, cnt, cnt - 1, k, v);
-    }
-    __syncthreads();
-    if (diag < cnt) {
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            if (diag + j < cnt) {
-                sm.k[pidx(diag + j)] = k[j];
-                sm.v[pidx(diag + j)] = v[j];
-            }
-        }
-    }
-    __syncthreads();
-    uint64_t* D = dk + out0;
-    uint32_t* Dv = dv ? dv + out0 : nullptr;
-#pragma unroll 4
-    for (int j = 0; j < ITEMS; ++j) {
-        int i = t + j * THREADS;
-        if (i < cnt) {
-            uint64_t key = sm.k[pidx(i)];
-            D[i] = decode_out ? decode_key(key, mode) : key;
-            if (Dv) Dv[i] = sm.v[pidx(i)];
-        }
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -460,107 +401,15 @@ __global__ void frog_partition_kernel(Slots sl, const FrogNode* __restrict__ lev
                              [&](int64_t j) { return *sl.kp(rb + j); });
 }
 
-// One in-place symmetric merge level.  A data-left node writes its output to
-// slots [r, r+n); the only inputs it can overwrite are its left run's elements
-// (they move right), so its chunks run from the top down (descending tickets)
-// and chunk c writes after every later chunk that reads the left-run elements
-// under it has loaded.  A data-right node (output [r+b, r+b+n)) is the mirror
-// image: its right run's elements move left, chunks run bottom up.  The right
-// (left) run of a data-left (data-right) node is never overwritten, because the
-// node holds at least as many buffer slots as its inner child has elements.
-template <int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS)
-    frog_merge_kernel(Slots sl, const FrogNode* __restrict__ level, const FrogNode* __restrict__ child,
-                      int64_t nnodes, int64_t nch, const int64_t* __restrict__ splits, int mode,
-                      int decode_out, int* ticket, int* loaded, int* call_err, uint64_t limit_ns,
-                      int64_t skip_ticket, const int* presorted)
-{
-    constexpr int C = THREADS * ITEMS;
-    if (skip_all(presorted)) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SmemKV<C>& sm = *reinterpret_cast<SmemKV<C>*>(smem_raw);
-    __shared__ int64_t s_tk;
-    __shared__ int s_ok;
-    const int t = threadIdx.x;
-    if (t == 0) s_tk = atomicAdd(ticket, 1);
-    __syncthreads();
-    const int64_t tk = s_tk;
-    const int64_t k = tk / nch, local = tk % nch;
-    const FrogNode x = level[k];
-    const int64_t c = x.side == 0 ? nch - 1 - local : local;
-    const int64_t fi = k * nch + c;
-    const int64_t w0 = c * C;
-    if (w0 >= x.n) {
-        if (t == 0 && tk != skip_ticket) st_release(&loaded[fi], 1);
-        return;
-    }
-    const FrogNode L = child[2 * k], R = child[2 * k + 1];
-    const int64_t w1 = imin64(w0 + C, x.n);
-    const int64_t a0 = splits[fi];
-    const int64_t a1 = (w1 == x.n) ? L.n : splits[fi + 1];
-    const int na = (int)(a1 - a0), nb = (int)((w1 - a1) - (w0 - a0));
-    const int cnt = na + nb;
-    const int64_t ra = frog_data_slot(L) + a0, rb = frog_data_slot(R) + (w0 - a0);
-#pragma unroll 4
-    for (int j = 0; j < ITEMS; ++j) {
-        int i = t + j * THREADS;
-        if (i < cnt) {
-            int64_t s = i < na ? ra + i : rb + (i - na);
-            sm.k[pidx(i)] = *sl.kp(s);
-            sm.v[pidx(i)] = sl.v0 ? *sl.vp(s) : 0u;
-        }
-    }
-    __syncthreads();
-    if (t == 0 && tk != skip_ticket) st_release(&loaded[fi], 1);
-    uint64_t kk[ITEMS];
-    uint32_t vv[ITEMS];
-    const int diag = t * ITEMS;
-    if (diag < cnt) {
-        int ai = (int)merge_path(
-            diag, na, nb, [&](int64_t q) { return sm.k[pidx((int)q)]; },
-            [&](int64_t q) { return sm.k[pidx(na + (int)q)]; });
-        serial_merge<C, ITEMS>(sm, ai, na, na + diag - ai, cnt, cnt - 1, kk, vv);
-    }
-    __syncthreads();
-    if (diag < cnt) {
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            if (diag + j < cnt) {
-                sm.k[pidx(diag + j)] = kk[j];
-                sm.v[pidx(diag + j)] = vv[j];
-            }
-        }
-    }
-    if (t == 0) {
-        bool ok = true;
-        const int64_t* sp = splits + k * nch;
-        if (x.side == 0) {
-            const int64_t lim = imin64(w1, L.n);   // left-run indices [w0, lim) are overwritten
-            if (w0 < lim)
-                for (int64_t c2 = c + 1; ok && c2 < nch && c2 * C < x.n && sp[c2] < lim; ++c2)
-                    ok = wait_flag(&loaded[k * nch + c2], 1, call_err, limit_ns, GNS_ERR_TIMEOUT);
-        } else {
-            const int64_t lo = imax64(w0 - L.n, 0);          // right-run indices [lo, hi)
-            const int64_t hi = imin64(w1 - L.n, R.n);
-            if (lo < hi)
-                for (int64_t c2 = c - 1; ok && c2 >= 0 && ((c2 + 1) * C - sp[c2 + 1]) > lo; --c2)
-                    ok = wait_flag(&loaded[k * nch + c2], 1, call_err, limit_ns, GNS_ERR_TIMEOUT);
-        }
-        s_ok = ok;
-    }
-    __syncthreads();
-    if (!s_ok) return;
-    const int64_t o = frog_data_slot(x) + w0;
-#pragma unroll 4
-    for (int j = 0; j < ITEMS; ++j) {
-        int i = t + j * THREADS;
-        if (i < cnt) {
-            uint64_t key = sm.k[pidx(i)];
-            *sl.kp(o + i) = decode_out ? decode_key(key, mode) : key;
-            if (sl.v0) *sl.vp(o + i) = sm.v[pidx(i)];
-        }
-    }
-}
+// One in-place symmetric merge level (kernel: frog_merge_tma_kernel).  A
+// data-left node writes its output to slots [r, r+n); the only inputs it can
+// overwrite are its left run's elements (they move right), so its chunks run
+// from the top down (descending tickets) and chunk c writes after every later
+// chunk that reads the left-run elements under it has loaded.  A data-right
+// node (output [r+b, r+b+n)) is the mirror image: its right run's elements move
+// left, chunks run bottom up.  The right (left) run of a data-left (data-right)
+// node is never overwritten, because the node holds at least as many buffer
+// slots as its inner child has elements.
 
 __global__ void publish_err_kernel(const int* call_err, int* status)
 {

@@ -16,15 +16,30 @@
 
 #include "gns_internal.h"
 #include "gns_kernels.cuh"
+#include "gns_merge_tma.cuh"
 
 namespace gns {
 
 namespace {
 
 constexpr size_t kSmemTile = sizeof(SmemKV<TILE>);
-constexpr size_t kSmemChunk = sizeof(SmemKV<CHUNK>);
+constexpr size_t kSmemTma = sizeof(MergeSmem<TMA_CHUNK>);
+
+int num_sms()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && cached[dev]) return cached[dev];
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (v <= 0) v = 152;
+    if (dev < 64) cached[dev] = v;
+    return v;
+}
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+int64_t imin(int64_t a, int64_t b) { return a < b ? a : b; }
 
 // Merge levels of the 100% tier: ceil(log2(#tiles)).
 int merge_levels(int64_t n)
@@ -48,7 +63,7 @@ int64_t frog_chunks(int64_t n, int d) { return ceil_div(ceil_div(n, 1ll << d), C
 
 struct Layout {
     // control words (ints): [0..1] presorted flags, [2] call error
-    size_t ctl, bufk, bufv, splits, nodes, flags, tickets, total;
+    size_t ctl, bufk, bufv, splits, deps, nodes, flags, tickets, total;
     size_t flags_bytes, tickets_bytes;
     int L, D;
 };
@@ -79,6 +94,7 @@ Layout make_layout(int64_t n, double bf, bool with_vals)
             nflags += e;
         }
         o.splits = off; off += align256((size_t)max_split * 8);
+        o.deps = off; off += align256((size_t)max_split * 8);
         o.flags = off; o.flags_bytes = align256((size_t)nflags * 4); off += o.flags_bytes;
         o.tickets = off; o.tickets_bytes = align256((size_t)(D + 1) * 4); off += o.tickets_bytes;
     }
@@ -98,9 +114,9 @@ void init_attributes()
 {
     std::call_once(g_attr_once, [] {
         set_smem(tile_sort_kernel<SORT_THREADS, SORT_ITEMS>, kSmemTile);
-        set_smem(merge_pass_kernel<MERGE_THREADS, MERGE_ITEMS>, kSmemChunk);
+        set_smem(merge_pass_tma_kernel<TMA_THREADS, TMA_ITEMS>, kSmemTma);
         set_smem(frog_setup_kernel<SORT_THREADS, SORT_ITEMS>, kSmemTile);
-        set_smem(frog_merge_kernel<MERGE_THREADS, MERGE_ITEMS>, kSmemChunk);
+        set_smem(frog_merge_tma_kernel<TMA_THREADS, TMA_ITEMS>, kSmemTma);
     });
 }
 
@@ -143,7 +159,8 @@ int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, 
 
     GNS_TRY(cudaMemsetAsync(ctl, 0, 256, s));
     GNS_TRY(cudaMemsetAsync(presorted, 1, 2 * sizeof(int), s));   // both flags "true"
-    GNS_TRY(launch(K_RUN_DETECT, run_detect_kernel, dim3((unsigned)ceil_div(n, DETECT_TILE)), dim3(256), 0, s,
+    GNS_TRY(launch(K_RUN_DETECT, run_detect_kernel, dim3((unsigned)imin(ceil_div(n, DETECT_TILE), 152 * 8)),
+                   dim3(256), 0, s,
                    (const uint64_t*)keys, n, mode, presorted));
     GNS_TRY(launch(K_REVERSE, reverse_kernel, dim3(152 * 8), dim3(256), 0, s, keys, vals, n, (const int*)presorted));
 
@@ -168,9 +185,11 @@ int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, 
             const int64_t w = (int64_t)TILE << lvl;
             GNS_TRY(launch(K_MERGE_PARTITION, merge_partition_kernel, dim3((unsigned)ceil_div(nblocks, 256)),
                            dim3(256), 0, s, (const uint64_t*)cur_k, n, w, nblocks, splits, skip));
-            GNS_TRY(launch(K_MERGE_PASS, merge_pass_kernel<MERGE_THREADS, MERGE_ITEMS>, dim3((unsigned)nblocks),
-                           dim3(MERGE_THREADS), kSmemChunk, s, (const uint64_t*)cur_k, (const uint32_t*)cur_v,
-                           oth_k, oth_v, n, w, (const int64_t*)splits, mode, (int)(lvl == L - 1), skip));
+            const int64_t grid = imin(nblocks, (int64_t)num_sms() * TMA_CTAS_PER_SM);
+            GNS_TRY(launch(K_MERGE_PASS, merge_pass_tma_kernel<TMA_THREADS, TMA_ITEMS>, dim3((unsigned)grid),
+                           dim3(TMA_THREADS), kSmemTma, s, (const uint64_t*)cur_k, (const uint32_t*)cur_v, oth_k,
+                           oth_v, n, w, nblocks, (const int64_t*)splits, mode, (int)(lvl == L - 1), call_err,
+                           wait_limit_ns(), skip));
             uint64_t* tk = cur_k; cur_k = oth_k; oth_k = tk;
             uint32_t* tv = cur_v; cur_v = oth_v; oth_v = tv;
         }
@@ -182,6 +201,7 @@ int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, 
         sl.v1 = vals ? (uint32_t*)(ws + lay.bufv) : nullptr;
         FrogNode* nodes = (FrogNode*)(ws + lay.nodes);
         int64_t* splits = (int64_t*)(ws + lay.splits);
+        int2* deps = (int2*)(ws + lay.deps);
         int* flags = (int*)(ws + lay.flags);
         int* tickets = (int*)(ws + lay.tickets);
         const uint64_t limit = wait_limit_ns();
@@ -203,9 +223,13 @@ int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, 
             const FrogNode* child = nodes + (2 * nnodes - 1);
             GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel, dim3((unsigned)ceil_div(nnodes * nch, 256)),
                            dim3(256), 0, s, sl, level, child, nnodes, nch, splits, skip));
-            GNS_TRY(launch(K_FROG_MERGE, frog_merge_kernel<MERGE_THREADS, MERGE_ITEMS>,
-                           dim3((unsigned)(nnodes * nch)), dim3(MERGE_THREADS), kSmemChunk, s, sl, level, child,
-                           nnodes, nch, (const int64_t*)splits, mode, (int)(d == 0), tickets + d, lflags, call_err,
+            GNS_TRY(launch(K_FROG_PARTITION, frog_deps_kernel, dim3((unsigned)ceil_div(nnodes * nch, 256)),
+                           dim3(256), 0, s, level, child, nnodes, nch, (const int64_t*)splits, deps, skip));
+            const int64_t grid = imin(nnodes * nch, (int64_t)num_sms() * TMA_CTAS_PER_SM);
+            GNS_TRY(launch(K_FROG_MERGE, frog_merge_tma_kernel<TMA_THREADS, TMA_ITEMS>, dim3((unsigned)grid),
+                           dim3(TMA_THREADS), kSmemTma, s, sl, level, child,
+                           nnodes, nch, (const int64_t*)splits, (const int2*)deps, mode, (int)(d == 0), tickets + d,
+                           lflags, call_err,
                            limit, skip_ticket, skip));
             skip_ticket = -1;
             lflags += nnodes * nch;
