@@ -50,7 +50,8 @@ enum {
     GNS_ERR_UNSUPPORTED = -2,  /* valid request this library does not serve  */
     GNS_ERR_OOM = -3,          /* the allocator returned NULL                 */
     GNS_ERR_CUDA = -4,         /* a CUDA runtime call or launch failed        */
-    GNS_ERR_TIMEOUT = -5       /* a device-side bounded wait ran out          */
+    GNS_ERR_TIMEOUT = -5,      /* a device-side bounded wait ran out          */
+    GNS_ERR_INTERNAL = -6      /* a device-side consistency check failed      */
 };
 
 /* Sort orders: the two stable API targets served (AscLeft, DescLeft). */

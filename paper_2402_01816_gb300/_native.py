@@ -17,6 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libgns.so")
 
 GNS_OK, GNS_ERR_INVALID, GNS_ERR_UNSUPPORTED, GNS_ERR_OOM, GNS_ERR_CUDA, GNS_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+GNS_ERR_INTERNAL = -6
 ASCENDING, DESCENDING = 0, 1
 KEY_F64, KEY_I64 = 0, 1
 WS_SORT, WS_LEARNED = 0, 1

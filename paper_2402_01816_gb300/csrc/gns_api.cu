@@ -294,6 +294,7 @@ const char* gns_strerror(int code)
         case GNS_ERR_OOM: return "workspace allocation failed";
         case GNS_ERR_CUDA: return "CUDA runtime error";
         case GNS_ERR_TIMEOUT: return "device-side wait timed out";
+        case GNS_ERR_INTERNAL: return "device-side consistency check failed";
         default: return "unknown error";
     }
 }

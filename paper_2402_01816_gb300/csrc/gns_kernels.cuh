@@ -143,7 +143,7 @@ __device__ void block_sort_smem(SmemKV<THREADS * ITEMS>& sm, int n_valid)
 // DETECT_TILE keys (one coalesced load per key, staged in shared memory with the
 // key before the tile) and stop as soon as both flags are cleared, so random
 // inputs cost about one wave.
-__global__ void __launch_bounds__(256) run_detect_kernel(const uint64_t* __restrict__ keys, int64_t n,
+static __global__ void __launch_bounds__(256) run_detect_kernel(const uint64_t* __restrict__ keys, int64_t n,
                                                          int mode, int* presorted)
 {
     __shared__ uint64_t sk[DETECT_TILE + 1];
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(256) run_detect_kernel(const uint64_t* __restr
 
 // Reverses a strictly decreasing array in place (Octosort's final reversal: the
 // reverse of a strictly ordered run is the stable sort, as it has no ties).
-__global__ void reverse_kernel(uint64_t* keys, uint32_t* vals, int64_t n, const int* presorted)
+static __global__ void reverse_kernel(uint64_t* keys, uint32_t* vals, int64_t n, const int* presorted)
 {
     if (presorted[0] != 0 || presorted[1] == 0) return;
     const int64_t half = n / 2;
@@ -194,9 +194,13 @@ __global__ void reverse_kernel(uint64_t* keys, uint32_t* vals, int64_t n, const 
     }
 }
 
-__device__ __forceinline__ bool skip_all(const int* presorted)
+// ctl[0..1]: presorted flags (nothing left to do), ctl[2]: the call's error
+// word.  Every kernel after run detection returns at once when any is set, so
+// that after a device-side error (a wait that ran out) no later pass runs on
+// data the failed pass left half-written.
+__device__ __forceinline__ bool skip_all(const int* ctl)
 {
-    return presorted != nullptr && (presorted[0] | presorted[1]) != 0;
+    return ctl != nullptr && (ctl[0] | ctl[1] | ld_relaxed(&ctl[2])) != 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -239,7 +243,7 @@ __global__ void __launch_bounds__(THREADS)
 
 // splits[b] = co-rank (A elements) of output position b*CHUNK within its pair of
 // runs of width w.
-__global__ void merge_partition_kernel(const uint64_t* __restrict__ k, int64_t n, int64_t w,
+static __global__ void merge_partition_kernel(const uint64_t* __restrict__ k, int64_t n, int64_t w,
                                        int64_t nblocks, int64_t* splits, const int* presorted)
 {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -298,7 +302,7 @@ struct Slots {
 
 // All nodes of depths 0..D in heap order: node k of depth d at (1 << d) - 1 + k.
 // Each thread walks from the root down the bits of k.
-__global__ void frog_plan_kernel(FrogNode* nodes, int64_t n, int D)
+static __global__ void frog_plan_kernel(FrogNode* nodes, int64_t n, int D)
 {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t total = (2ll << D) - 1;
@@ -387,7 +391,7 @@ __global__ void __launch_bounds__(THREADS)
 }
 
 // splits[k*nch + c] = co-rank (left-run elements) of output c*CHUNK of node k.
-__global__ void frog_partition_kernel(Slots sl, const FrogNode* __restrict__ level,
+static __global__ void frog_partition_kernel(Slots sl, const FrogNode* __restrict__ level,
                                       const FrogNode* __restrict__ child, int64_t nnodes, int64_t nch,
                                       int64_t* splits, const int* presorted)
 {
@@ -411,7 +415,7 @@ __global__ void frog_partition_kernel(Slots sl, const FrogNode* __restrict__ lev
 // node is never overwritten, because the node holds at least as many buffer
 // slots as its inner child has elements.
 
-__global__ void publish_err_kernel(const int* call_err, int* status)
+static __global__ void publish_err_kernel(const int* call_err, int* status)
 {
     int e = *call_err;
     if (e != 0) atomicCAS(status, 0, e);

@@ -290,6 +290,10 @@ __global__ void __launch_bounds__(THREADS)
     bool pending[2] = {false, false};
     auto stage = [&](int slot, int64_t blk) {
         ChunkGeo cg = merge_chunk_geo<C>(blk, n, w, splits);
+        if (cg.na < 0 || cg.nb < 0 || cg.na + cg.nb > C) {   // splits inconsistent: stage nothing
+            if (t == 0) atomicCAS(call_err, 0, GNS_ERR_INTERNAL);
+            cg.na = cg.nb = 0;
+        }
         StagedChunk g = stage_chunk<C>(sm.in[slot], &bars[slot], sk + cg.a_src, has_vals ? sv + cg.a_src : nullptr,
                                        cg.na, sk + cg.b_src, has_vals ? sv + cg.b_src : nullptr, cg.nb, nullptr, 0,
                                        nullptr, 0);
@@ -309,6 +313,7 @@ __global__ void __launch_bounds__(THREADS)
                 atomicCAS(call_err, 0, GNS_ERR_TIMEOUT);
                 s_ok = 0;
             }
+            if (ld_relaxed(call_err) != 0) s_ok = 0;
             bulk_wait_read_all();                     // previous chunk's bulk store has read `out`
         }
         parity[cur] ^= 1u;
@@ -437,7 +442,7 @@ __device__ __forceinline__ int2 frog_dep_range(int64_t c, const FrogNode& x, con
 
 // deps[k * nch + c] = frog_dep_range for every chunk of a level (after the
 // partition, before the merge).
-__global__ void frog_deps_kernel(const FrogNode* __restrict__ level, const FrogNode* __restrict__ child,
+static __global__ void frog_deps_kernel(const FrogNode* __restrict__ level, const FrogNode* __restrict__ child,
                                  int64_t nnodes, int64_t nch, const int64_t* __restrict__ splits, int2* deps,
                                  const int* presorted)
 {
@@ -512,6 +517,11 @@ __global__ void __launch_bounds__(THREADS)
             nb = (int)((fc.w1 - a1) - (fc.w0 - a0));
             ra = frog_data_slot(L) + a0;
             rb = frog_data_slot(R) + (fc.w0 - a0);
+            if (na < 0 || nb < 0 || na + nb > C || a0 < 0 || a1 > L.n) {   // splits inconsistent
+                if (t == 0) atomicCAS(call_err, 0, GNS_ERR_INTERNAL);
+                na = nb = 0;
+                ra = rb = 0;
+            }
         }
         // slices that straddle the caller-array / buffer boundary use plain loads
         const bool pa = na > 0 && ra < sl.n && ra + na > sl.n;
@@ -547,6 +557,7 @@ __global__ void __launch_bounds__(THREADS)
             } else if (tk != skip_ticket && !published_cur) {
                 st_release(&loaded[cur.fi], 1);         // this chunk's inputs are in shared memory
             }
+            if (ld_relaxed(call_err) != 0) s_ok = 0;
             bulk_wait_read_all();
         }
         bool published_next = false;
