@@ -133,6 +133,38 @@ int gns_segmented_sort_ex(void* keys, int key_type, uint32_t* payload,
                           const int64_t* offsets, int64_t nseg, int64_t total_n,
                           int order, gns_stream_t stream);
 
+/*
+ * gns_sort_noalloc -- gns_sort at the 100% buffer tier that allocates nothing.
+ * (The paper has no counterpart: this is a service for callers, not a step of
+ * the method.)
+ *
+ * Some callers cannot allocate device memory when they need a sort: code that
+ * runs while somebody else is capturing a CUDA graph (an allocation there is
+ * either illegal or becomes part of the graph), latency-critical or signal-safe
+ * paths that forbid allocator calls, and hosts that own all device memory and
+ * hand a library only the buffers it works on.  This entry point calls no
+ * cudaMalloc, cudaFree, stream-ordered allocator or allocator hook.  Its
+ * scratch is one fixed device array inside this library, sized for
+ * GNS_NOALLOC_MAX_N elements (about 12 MiB); every GPU that loads the library
+ * holds that array until the process exits.
+ *
+ * Arguments as gns_sort for float64 keys (device keys, device payload or NULL,
+ * n, order); the result is the same stable sort, bit for bit.
+ * Errors: GNS_ERR_UNSUPPORTED when n > GNS_NOALLOC_MAX_N (use gns_sort),
+ * GNS_ERR_INVALID for bad arguments, GNS_ERR_CUDA if a launch fails.
+ *
+ * Set-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture that might include later calls.
+ * Sharing: every call on a device uses the same array and the array keeps the
+ * last call's contents (the call resets what must start at zero).  Calls that
+ * overlap on the GPU -- on different streams, or from different host threads
+ * without ordering -- race on the array and corrupt each other's results.
+ */
+#define GNS_NOALLOC_MAX_N (1 << 20)
+int gns_sort_noalloc(double* keys, uint32_t* payload, int64_t n, int order,
+                     gns_stream_t stream);
+
 /* Size in bytes of the scratch a call allocates.  kind = GNS_WS_SORT for
  * gns_sort at this buffer_fraction, GNS_WS_LEARNED for gns_learned_sort. */
 size_t gns_workspace_bytes(int64_t n, double buffer_fraction, int kind);

@@ -47,6 +47,7 @@ def lib() -> ctypes.CDLL:
                 "gns_sort": ([P, P, i64, i32, f64, P], i32),
                 "gns_sort_i64": ([P, P, i64, i32, f64, P], i32),
                 "gns_sort_host": ([P, P, i64, i32, i32, f64, P], i32),
+                "gns_sort_noalloc": ([P, P, i64, i32, P], i32),
                 "gns_segmented_sort": ([P, P, P, i64, P], i32),
                 "gns_segmented_sort_ex": ([P, i32, P, P, i64, i64, i32, P], i32),
                 "gns_workspace_bytes": ([i64, f64, i32], ctypes.c_size_t),
@@ -135,6 +136,20 @@ def gns_sort_host(keys: np.ndarray, payload: np.ndarray | None = None, order: in
     pp = None if payload is None else ctypes.c_void_p(payload.ctypes.data)
     _check(lib().gns_sort_host(ctypes.c_void_p(keys.ctypes.data), pp, keys.size, kt, order,
                                float(buffer_fraction), _stream(stream)), "gns_sort_host")
+
+
+NOALLOC_MAX_N = 1 << 20
+
+
+def gns_sort_noalloc(keys, payload=None, order: int = ASCENDING, stream=None) -> None:
+    """gns_sort_noalloc: the 100%-buffer sort of float64 keys using the library's
+    fixed scratch array instead of any allocation (n <= NOALLOC_MAX_N)."""
+    import torch
+    n = keys.numel()
+    if payload is not None and payload.numel() != n:
+        raise ValueError("payload must have as many elements as keys")
+    _check(lib().gns_sort_noalloc(_dev_ptr(keys, torch.float64, "keys"), _dev_ptr(payload, torch.int32, "payload"),
+                                  n, order, _stream(stream)), "gns_sort_noalloc")
 
 
 def gns_segmented_sort(keys, payload, offsets, order: int = ASCENDING, stream=None) -> None:
