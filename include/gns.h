@@ -165,6 +165,23 @@ int gns_segmented_sort_ex(void* keys, int key_type, uint32_t* payload,
 int gns_sort_noalloc(double* keys, uint32_t* payload, int64_t n, int order,
                      gns_stream_t stream);
 
+/*
+ * Segmented-sort schedule.  The first call for a (total length, segment count,
+ * offsets pointer) times the candidate size-class schedules on a scratch copy
+ * of the input (synchronising the stream) and keeps the fastest; the call then
+ * captures its whole kernel sequence into a CUDA graph, cached with its
+ * workspace for these pointers (up to four graphs; the oldest is released).
+ * Later calls replay the graph.  Set GNS_SEG_SCHEDULE=0|1|2 to skip tuning.
+ *   gns_segmented_schedule: index of the tuned schedule for this shape
+ *     (0 = one 4096-key tile shape for every segment, 1 = segments of up to 1024
+ *     keys sorted by 64-thread CTAs, 2 = up to 2048 keys by 128-thread CTAs),
+ *     or -1 if none was tuned yet.
+ *   gns_segmented_release: synchronises `stream`, destroys the cached graphs and
+ *     frees their workspace, and forgets the tuned schedules.
+ */
+int gns_segmented_schedule(int64_t total_n, int64_t nseg, const int64_t* offsets);
+void gns_segmented_release(gns_stream_t stream);
+
 /* Size in bytes of the scratch a call allocates.  kind = GNS_WS_SORT for
  * gns_sort at this buffer_fraction, GNS_WS_LEARNED for gns_learned_sort. */
 size_t gns_workspace_bytes(int64_t n, double buffer_fraction, int kind);

@@ -8,6 +8,7 @@ seeded synthetic workloads.
 """
 from ._native import (ASCENDING, DESCENDING, GNS_ERR_CUDA, GNS_ERR_INVALID, GNS_ERR_OOM,  # noqa: F401
                       GNS_ERR_TIMEOUT, GNS_ERR_UNSUPPORTED, GNS_OK, GnsError, gns_debug_skip_publish,
-                      gns_launch_count, gns_profile_enable, gns_profile_read, gns_segmented_sort,
+                      gns_launch_count, gns_profile_enable, gns_profile_read, gns_segmented_release,
+                      gns_segmented_schedule, gns_segmented_sort, gns_sort_noalloc,
                       gns_set_wait_limit_ns, gns_sort, gns_sort_host, gns_stream_status, gns_version,
                       gns_workspace_bytes, lib)

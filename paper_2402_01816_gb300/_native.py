@@ -51,6 +51,8 @@ def lib() -> ctypes.CDLL:
                 "gns_segmented_sort": ([P, P, P, i64, P], i32),
                 "gns_segmented_sort_ex": ([P, i32, P, P, i64, i64, i32, P], i32),
                 "gns_workspace_bytes": ([i64, f64, i32], ctypes.c_size_t),
+                "gns_segmented_schedule": ([i64, i64, P], i32),
+                "gns_segmented_release": ([P], None),
                 "gns_set_allocator": ([P, P, P], None),
                 "gns_stream_status": ([P], i32),
                 "gns_release_workspace_cache": ([], i32),
@@ -168,6 +170,14 @@ def gns_segmented_sort(keys, payload, offsets, order: int = ASCENDING, stream=No
                                        _dev_ptr(payload, torch.int32, "payload"),
                                        _dev_ptr(offsets, torch.int64, "offsets"), nseg, keys.numel(),
                                        order, _stream(stream)), "gns_segmented_sort")
+
+
+def gns_segmented_schedule(total_n: int, offsets) -> int:
+    return int(lib().gns_segmented_schedule(total_n, offsets.numel() - 1, ctypes.c_void_p(offsets.data_ptr())))
+
+
+def gns_segmented_release(stream=None) -> None:
+    lib().gns_segmented_release(_stream(stream))
 
 
 def gns_workspace_bytes(n: int, buffer_fraction: float = 1.0, kind: int = WS_SORT) -> int:

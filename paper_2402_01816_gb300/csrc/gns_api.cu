@@ -137,6 +137,8 @@ std::vector<ProfRec> g_prof_recs;
 std::vector<cudaEvent_t> g_event_pool;
 thread_local int g_pending_kid = -1;
 thread_local cudaEvent_t g_pending_a = nullptr;
+thread_local bool g_capturing = false;
+thread_local uint64_t g_captured = 0;
 
 cudaEvent_t take_event()
 {
@@ -151,10 +153,29 @@ cudaEvent_t take_event()
 }
 }  // namespace
 
+void set_capturing(bool on)
+{
+    g_capturing = on;
+    if (on) g_captured = 0;
+}
+
+void count_launch()
+{
+    if (g_capturing) ++g_captured;
+    else g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+uint64_t take_captured_launches()
+{
+    uint64_t c = g_captured;
+    g_captured = 0;
+    return c;
+}
+
 void prof_before(int kid, cudaStream_t s)
 {
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    if (!g_prof_on) return;
+    if (!g_prof_on || g_capturing) return;
     g_pending_kid = kid;
     g_pending_a = take_event();
     cudaEventRecord(g_pending_a, s);
@@ -163,7 +184,7 @@ void prof_before(int kid, cudaStream_t s)
 void prof_after(cudaStream_t s)
 {
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    if (!g_prof_on || g_pending_kid < 0) return;
+    if (!g_prof_on || g_capturing || g_pending_kid < 0) return;
     cudaEvent_t b = take_event();
     cudaEventRecord(b, s);
     g_prof_recs.push_back({g_pending_kid, g_pending_a, b});

@@ -44,6 +44,12 @@ enum KernelId {
 void prof_before(int kid, cudaStream_t s);
 void prof_after(cudaStream_t s);
 extern std::atomic<uint64_t> g_launches;
+// While a graph is being captured on this thread, launches are counted into the
+// graph (and added to g_launches each time the graph is launched) and not
+// bracketed by profiling events.
+void set_capturing(bool on);
+void count_launch();
+uint64_t take_captured_launches();
 
 template <typename Kernel, typename... Args>
 inline cudaError_t launch(int kid, Kernel kernel, dim3 grid, dim3 block, size_t smem,
@@ -54,7 +60,7 @@ inline cudaError_t launch(int kid, Kernel kernel, dim3 grid, dim3 block, size_t 
     kernel<<<grid, block, smem, s>>>(args...);
     cudaError_t e = cudaGetLastError();
     prof_after(s);
-    g_launches.fetch_add(1, std::memory_order_relaxed);
+    count_launch();
     return e;
 }
 
@@ -82,5 +88,10 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 int sort_device(uint64_t* keys, uint32_t* payload, int64_t n, int mode,
                 double buffer_fraction, cudaStream_t s);
 size_t sort_workspace_bytes(int64_t n, double buffer_fraction);
+
+// Segmented sort core and helpers (gns_segmented.cu).
+int segmented_sort_device(uint64_t* keys, uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, int mode,
+                          cudaStream_t s);
+size_t segmented_workspace_bytes(int64_t n, int64_t nseg);
 
 }  // namespace gns

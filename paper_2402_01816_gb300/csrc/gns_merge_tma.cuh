@@ -261,25 +261,29 @@ __device__ __forceinline__ bool bulk_ok(const void* Dk, const void* Dv, int cnt)
     return ((uintptr_t)Dk & 15) == 0 && (cnt & 3) == 0 && (Dv == nullptr || ((uintptr_t)Dv & 15) == 0);
 }
 
-// ============================================================ 100% tier
-template <int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS)
-    merge_pass_tma_kernel(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sv, uint64_t* __restrict__ dk,
-                          uint32_t* __restrict__ dv, int64_t n, int64_t w, int64_t nblocks,
-                          const int64_t* __restrict__ splits, int mode, int decode_out, int* call_err,
-                          uint64_t limit_ns, const int* presorted)
+// ============================================================ ping-pong levels
+// One staged chunk: two input slices and where the merged run goes.
+struct MergeItem {
+    const uint64_t* ak; const uint32_t* av; int na;
+    const uint64_t* bk; const uint32_t* bv; int nb;
+    uint64_t* dk; uint32_t* dv;
+    int decode;
+};
+
+// The pipeline shared by every out-of-place merge level: items b = blockIdx.x,
+// blockIdx.x + gridDim.x, ... < nitems, described by get(b).
+template <int THREADS, int ITEMS, typename Get>
+__device__ __forceinline__ void merge_items_tma(int64_t nitems, Get get, int mode, int* call_err, uint64_t limit_ns)
 {
     constexpr int C = THREADS * ITEMS;
-    if (skip_all(presorted)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MergeSmem<C>& sm = *reinterpret_cast<MergeSmem<C>*>(smem_raw);
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ StagedChunk staged[2];
     __shared__ int s_ok;
     const int t = threadIdx.x;
-    const bool has_vals = sv != nullptr;
     int64_t b = blockIdx.x;
-    if (b >= nblocks) return;
+    if (b >= nitems) return;
     if (t == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -288,50 +292,53 @@ __global__ void __launch_bounds__(THREADS)
     }
     __syncthreads();
     bool pending[2] = {false, false};
-    auto stage = [&](int slot, int64_t blk) {
-        ChunkGeo cg = merge_chunk_geo<C>(blk, n, w, splits);
-        if (cg.na < 0 || cg.nb < 0 || cg.na + cg.nb > C) {   // splits inconsistent: stage nothing
+    auto stage = [&](int slot, const MergeItem& m) {
+        int na = m.na, nb = m.nb;
+        if (na < 0 || nb < 0 || na + nb > C) {   // inconsistent splits: stage nothing
             if (t == 0) atomicCAS(call_err, 0, GNS_ERR_INTERNAL);
-            cg.na = cg.nb = 0;
+            na = nb = 0;
         }
-        StagedChunk g = stage_chunk<C>(sm.in[slot], &bars[slot], sk + cg.a_src, has_vals ? sv + cg.a_src : nullptr,
-                                       cg.na, sk + cg.b_src, has_vals ? sv + cg.b_src : nullptr, cg.nb, nullptr, 0,
+        StagedChunk g = stage_chunk<C>(sm.in[slot], &bars[slot], m.ak, m.av, na, m.bk, m.bv, nb, nullptr, 0,
                                        nullptr, 0);
-        pending[slot] = true;
         if (t == 0) staged[slot] = g;
-        return cg.out0;
+        pending[slot] = true;
     };
-    int64_t out_cur = stage(0, b);
+    MergeItem cur = get(b);
+    stage(0, cur);
     unsigned parity[2] = {0u, 0u};
-    for (int it = 0; b < nblocks; ++it, b += gridDim.x) {
-        const int cur = it & 1;
+    for (int it = 0; b < nitems; ++it, b += gridDim.x) {
+        const int cs = it & 1;
         const int64_t nb_ = b + gridDim.x;
-        int64_t out_nxt = 0;
-        if (nb_ < nblocks) out_nxt = stage(cur ^ 1, nb_);
+        MergeItem nxt = cur;
+        if (nb_ < nitems) {
+            nxt = get(nb_);
+            stage(cs ^ 1, nxt);
+        }
         if (t == 0) {
-            if (!mbar_wait(&bars[cur], parity[cur], limit_ns)) {
+            if (!mbar_wait(&bars[cs], parity[cs], limit_ns)) {
                 atomicCAS(call_err, 0, GNS_ERR_TIMEOUT);
                 s_ok = 0;
             }
             if (ld_relaxed(call_err) != 0) s_ok = 0;
             bulk_wait_read_all();                     // previous chunk's bulk store has read `out`
         }
-        parity[cur] ^= 1u;
-        pending[cur] = false;
+        parity[cs] ^= 1u;
+        pending[cs] = false;
         __syncthreads();
         if (!s_ok) break;
-        const StagedChunk g = staged[cur];
+        const StagedChunk g = staged[cs];
+        const bool has_vals = cur.av != nullptr;
         uint64_t k[ITEMS];
         uint32_t v[ITEMS];
-        const int m = merge_staged<C, ITEMS>(sm.in[cur], g, k, v, has_vals);
-        if (m > 0) write_out<C, ITEMS>(sm.out, k, v, m, has_vals, mode, decode_out);
+        const int m = merge_staged<C, ITEMS>(sm.in[cs], g, k, v, has_vals);
+        if (m > 0) write_out<C, ITEMS>(sm.out, k, v, m, has_vals, mode, cur.decode);
         fence_proxy_async_shared();
         __syncthreads();
         const int cnt = g.na + g.nb;
-        uint64_t* Dk = dk + out_cur;
-        uint32_t* Dv = has_vals ? dv + out_cur : nullptr;
+        uint64_t* Dk = cur.dk;
+        uint32_t* Dv = has_vals ? cur.dv : nullptr;
         if (bulk_ok(Dk, Dv, cnt)) {
-            if (t == 0) {
+            if (t == 0 && cnt > 0) {
                 bulk_store(Dk, sm.out.k, (unsigned)cnt * 8);
                 if (Dv) bulk_store(Dv, sm.out.v, (unsigned)cnt * 4);
                 bulk_commit();
@@ -342,7 +349,7 @@ __global__ void __launch_bounds__(THREADS)
                 if (Dv) Dv[e] = sm.out.v[e];
             }
         }
-        out_cur = out_nxt;
+        cur = nxt;
     }
     if (t == 0) {
         bulk_wait_all();
@@ -350,6 +357,29 @@ __global__ void __launch_bounds__(THREADS)
         for (int q = 0; q < 2; ++q)
             if (pending[q]) mbar_wait(&bars[q], parity[q], limit_ns);
     }
+}
+
+// One Nocopy merge level of the 100% tier: runs of width w in (sk, sv) merged
+// pairwise into (dk, dv), chunk b = outputs [b*C, (b+1)*C).
+template <int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS)
+    merge_pass_tma_kernel(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sv, uint64_t* __restrict__ dk,
+                          uint32_t* __restrict__ dv, int64_t n, int64_t w, int64_t nblocks,
+                          const int64_t* __restrict__ splits, int mode, int decode_out, int* call_err,
+                          uint64_t limit_ns, const int* presorted)
+{
+    constexpr int C = THREADS * ITEMS;
+    if (skip_all(presorted)) return;
+    auto get = [&](int64_t b) {
+        ChunkGeo cg = merge_chunk_geo<C>(b, n, w, splits);
+        MergeItem m;
+        m.ak = sk + cg.a_src; m.av = sv ? sv + cg.a_src : nullptr; m.na = cg.na;
+        m.bk = sk + cg.b_src; m.bv = sv ? sv + cg.b_src : nullptr; m.nb = cg.nb;
+        m.dk = dk + cg.out0; m.dv = dv ? dv + cg.out0 : nullptr;
+        m.decode = decode_out;
+        return m;
+    };
+    merge_items_tma<THREADS, ITEMS>(nblocks, get, mode, call_err, limit_ns);
 }
 
 // ============================================================ <= 50% tier

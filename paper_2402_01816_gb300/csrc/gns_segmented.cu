@@ -1,21 +1,579 @@
-// gns_segmented.cu -- batched segmented sort (placeholder entry points).
+// gns_segmented.cu -- batched segmented stable sort (no counterpart in the paper:
+// a batching form of the same mergesort).
+//
+// Every segment [offsets[s], offsets[s+1]) is sorted independently, all of them
+// in one CUDA-graph launch:
+//   plan      per segment: tiles, merge levels k_s = ceil(log2(#tiles)), and the
+//             number of merge chunks it contributes to each level; one exclusive
+//             scan per row gives every kernel its work list on the device.
+//   tiles     size classes: segments up to the small-class bound are sorted by a
+//             smaller CTA shape (one tile each); all other segments are cut into
+//             4096-element tiles.  A segment with an odd number of levels writes
+//             its tiles to the buffer, so that its last level lands in `keys`
+//             (the merge decides where the data lies, as Omitsort does in the
+//             "Full adaptivity" section); a one-tile segment is done here.
+//   levels    level p merges the segments with k_s > p only: a partition kernel
+//             writes each 1024-output chunk's slices, the TMA merge pipeline of
+//             the plain sort consumes the list.
+// The whole sequence is captured once per (pointers, sizes, order, stream's
+// device, tuned schedule) and replayed; the tuned schedule (small-class bound
+// and its CTA shape) is picked by timing the candidates on a scratch copy the
+// first time a shape is seen.
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
 #include "gns_internal.h"
+#include "gns_kernels.cuh"
+#include "gns_merge_tma.cuh"
+
+namespace gns {
+
+namespace {
+
+constexpr int SEG_T = TILE;        // tile of the big class (4096)
+
+struct SegChunk {
+    int64_t out0, a_src, b_src;    // absolute positions
+    int32_t na, nb;
+    int32_t flags;                 // bit 0: read the buffer (else keys); bit 1: last level (decode)
+    int32_t pad;
+};
+
+// ---------------------------------------------------------------- plan
+// rows (each nseg + 1 long): row 0 = small-class tiles, row 1 = big-class tiles,
+// row 2 + p = merge chunks of level p.
+__global__ void seg_count_kernel(const int64_t* __restrict__ off, int64_t nseg, int L, int64_t small_max,
+                                 int64_t* rows, uint8_t* levels, const int* ctl)
+{
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg || skip_all(ctl)) return;
+    const int64_t stride = nseg + 1;
+    const int64_t len = off[s + 1] - off[s];
+    const int64_t tiles = (len + SEG_T - 1) / SEG_T;
+    int k = 0;
+    while ((1ll << k) < tiles) ++k;
+    levels[s] = (uint8_t)k;
+    const bool small = len > 0 && len <= small_max;
+    rows[s] = small ? 1 : 0;
+    rows[stride + s] = small ? 0 : tiles;
+    const int64_t chunks = (len + CHUNK - 1) / CHUNK;
+    for (int p = 0; p < L; ++p) rows[(2 + p) * stride + s] = k > p ? chunks : 0;
+}
+
+// Exclusive scan of row blockIdx.x in place; the total goes to entry nseg.
+__global__ void __launch_bounds__(1024) seg_scan_kernel(int64_t* rows, int64_t nseg, const int* ctl)
+{
+    if (skip_all(ctl)) return;
+    __shared__ int64_t warp_sum[32];
+    __shared__ int64_t s_carry;
+    int64_t* row = rows + (int64_t)blockIdx.x * (nseg + 1);
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    if (t == 0) s_carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nseg; base += 1024) {
+        const int64_t i = base + t;
+        const int64_t v = i < nseg ? row[i] : 0;
+        int64_t x = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        if (lane == 31) warp_sum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int64_t w = warp_sum[lane];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                int64_t y = __shfl_up_sync(0xffffffffu, w, d);
+                if (lane >= d) w += y;
+            }
+            warp_sum[lane] = w;                 // inclusive over warps
+        }
+        __syncthreads();
+        const int64_t incl = x + (wid > 0 ? warp_sum[wid - 1] : 0);
+        const int64_t carry = s_carry;
+        if (i < nseg) row[i] = carry + incl - v;
+        __syncthreads();
+        if (t == 1023) s_carry = carry + incl;
+        __syncthreads();
+    }
+    if (t == 0) row[nseg] = s_carry;
+}
+
+// Largest s in [0, nseg) with prefix[s] <= i (prefix non-decreasing, i < prefix[nseg]).
+__device__ __forceinline__ int64_t seg_of(const int64_t* prefix, int64_t nseg, int64_t i)
+{
+    int64_t lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------- tiles
+// Persistent: work item i of the row = tile (i - prefix[s]) of segment s.
+// big == 0: the row counts one tile per small segment (sorted whole).
+template <int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS)
+    seg_tile_kernel(uint64_t* keys, uint32_t* vals, uint64_t* bufk, uint32_t* bufv, const int64_t* __restrict__ off,
+                    int64_t nseg, const int64_t* __restrict__ prefix, const uint8_t* __restrict__ levels, int mode,
+                    const int* ctl)
+{
+    constexpr int T = THREADS * ITEMS;
+    if (skip_all(ctl)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemKV<T>& sm = *reinterpret_cast<SmemKV<T>*>(smem_raw);
+    __shared__ int64_t s_base, s_seg_end;
+    __shared__ int s_k;
+    const int t = threadIdx.x;
+    const int64_t total = prefix[nseg];
+    for (int64_t i = blockIdx.x; i < total; i += gridDim.x) {
+        if (t == 0) {
+            const int64_t s = seg_of(prefix, nseg, i);
+            s_base = off[s] + (i - prefix[s]) * T;
+            s_seg_end = off[s + 1];
+            s_k = levels[s];
+        }
+        __syncthreads();
+        const int64_t base = s_base;
+        const int nv = (int)imin64(T, s_seg_end - base);
+        const int k = s_k;
+#pragma unroll 4
+        for (int j = 0; j < ITEMS; ++j) {
+            int e = t + j * THREADS;
+            bool ok = e < nv;
+            sm.k[pidx(e)] = ok ? encode_key(keys[base + e], mode) : ~0ull;
+            sm.v[pidx(e)] = (ok && vals) ? vals[base + e] : 0u;
+        }
+        block_sort_smem<THREADS, ITEMS>(sm, nv);
+        uint64_t* dk = (k & 1) ? bufk : keys;
+        uint32_t* dv = (k & 1) ? bufv : vals;
+#pragma unroll 4
+        for (int j = 0; j < ITEMS; ++j) {
+            int e = t + j * THREADS;
+            if (e < nv) {
+                uint64_t key = sm.k[pidx(e)];
+                dk[base + e] = k == 0 ? decode_key(key, mode) : key;
+                if (dv) dv[base + e] = sm.v[pidx(e)];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- levels
+// One thread per work item of level p: its segment, its chunk and both
+// merge-path splits, written to list[i].
+__global__ void seg_partition_kernel(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ bufk,
+                                     const int64_t* __restrict__ off, int64_t nseg, const int64_t* __restrict__ prefix,
+                                     const uint8_t* __restrict__ levels, int p, SegChunk* list, const int* ctl)
+{
+    if (skip_all(ctl)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= prefix[nseg]) return;
+    const int64_t s = seg_of(prefix, nseg, i);
+    const int64_t c = i - prefix[s];
+    const int64_t seg0 = off[s], len = off[s + 1] - seg0;
+    const int k = levels[s];
+    const int from_buf = (k - p) & 1;
+    const uint64_t* src = (from_buf ? bufk : keys) + seg0;
+    const int64_t w = (int64_t)SEG_T << p;
+    const int64_t o = c * CHUNK;
+    const int64_t ps = (o / (2 * w)) * (2 * w);
+    const int64_t lenA = imin64(w, len - ps), lenB = imax64(0, imin64(w, len - ps - w));
+    const int64_t d0 = o - ps, d1 = imin64(d0 + CHUNK, lenA + lenB);
+    const uint64_t* A = src + ps;
+    const uint64_t* B = A + lenA;
+    auto ga = [&](int64_t x) { return A[x]; };
+    auto gb = [&](int64_t x) { return B[x]; };
+    const int64_t a0 = merge_path(d0, lenA, lenB, ga, gb);
+    const int64_t a1 = merge_path(d1, lenA, lenB, ga, gb);
+    SegChunk r;
+    r.out0 = seg0 + o;
+    r.a_src = seg0 + ps + a0;
+    r.b_src = seg0 + ps + lenA + (d0 - a0);
+    r.na = (int32_t)(a1 - a0);
+    r.nb = (int32_t)((d1 - a1) - (d0 - a0));
+    r.flags = from_buf | ((p == k - 1) ? 2 : 0);
+    r.pad = 0;
+    list[i] = r;
+}
+
+template <int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS)
+    seg_merge_tma_kernel(uint64_t* keys, uint32_t* vals, uint64_t* bufk, uint32_t* bufv,
+                         const SegChunk* __restrict__ list, const int64_t* __restrict__ count, int mode,
+                         int* call_err, uint64_t limit_ns, const int* ctl)
+{
+    if (skip_all(ctl)) return;
+    auto get = [&](int64_t i) {
+        const SegChunk r = list[i];
+        const bool fb = r.flags & 1;
+        const uint64_t* sk = fb ? bufk : keys;
+        const uint32_t* sv = fb ? bufv : vals;
+        uint64_t* dk = fb ? keys : bufk;
+        uint32_t* dv = fb ? vals : bufv;
+        MergeItem m;
+        m.ak = sk + r.a_src; m.av = sv ? sv + r.a_src : nullptr; m.na = r.na;
+        m.bk = sk + r.b_src; m.bv = sv ? sv + r.b_src : nullptr; m.nb = r.nb;
+        m.dk = dk + r.out0; m.dv = dv ? dv + r.out0 : nullptr;
+        m.decode = (r.flags >> 1) & 1;
+        return m;
+    };
+    merge_items_tma<THREADS, ITEMS>(*count, get, mode, call_err, limit_ns);
+}
+
+// ---------------------------------------------------------------- host side
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+int num_sms_dev()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 152;
+}
+
+// Schedules the autotuner chooses from: small-class bound and its CTA shape.
+struct SegSchedule {
+    int64_t small_max;   // 0: no small class
+    int small_threads;   // 64 (x16 = 1024 keys) or 128 (x16 = 2048 keys)
+};
+const SegSchedule kCandidates[] = {{0, 0}, {1024, 64}, {2048, 128}};
+
+int max_levels(int64_t n)
+{
+    int64_t tiles = ceil_div(n, SEG_T);
+    int L = 0;
+    while ((1ll << L) < tiles) ++L;
+    return L;
+}
+
+struct SegLayout {
+    size_t ctl, bufk, bufv, rows, levels, list, total;
+    int L;
+    int64_t max_items;
+};
+
+SegLayout seg_layout(int64_t n, int64_t nseg, bool with_vals)
+{
+    SegLayout o{};
+    size_t off = 0;
+    o.L = max_levels(n);
+    o.max_items = ceil_div(n, CHUNK) + nseg;
+    o.ctl = off; off += 256;
+    o.bufk = off; off += align256((size_t)n * 8);
+    o.bufv = off; off += with_vals ? align256((size_t)n * 4) : 0;
+    o.rows = off; off += align256((size_t)(2 + o.L) * (size_t)(nseg + 1) * 8);
+    o.levels = off; off += align256((size_t)nseg);
+    o.list = off; off += align256((size_t)o.max_items * sizeof(SegChunk));
+    o.total = off;
+    return o;
+}
+
+std::once_flag g_seg_attr_once;
+void seg_init_attributes()
+{
+    std::call_once(g_seg_attr_once, [] {
+        cudaFuncSetAttribute(seg_tile_kernel<256, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(SmemKV<4096>));
+        cudaFuncSetAttribute(seg_tile_kernel<128, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(SmemKV<2048>));
+        cudaFuncSetAttribute(seg_tile_kernel<64, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(SmemKV<1024>));
+        cudaFuncSetAttribute(seg_merge_tma_kernel<TMA_THREADS, TMA_ITEMS>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MergeSmem<TMA_CHUNK>));
+    });
+}
+
+// Enqueues the whole segmented sort on s (keys/vals in place, ws laid out by lay).
+cudaError_t seg_enqueue(uint64_t* keys, uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, int mode,
+                        const SegSchedule& sch, char* ws, const SegLayout& lay, cudaStream_t s)
+{
+    int* ctl = (int*)(ws + lay.ctl);
+    int* call_err = ctl + 2;
+    uint64_t* bufk = (uint64_t*)(ws + lay.bufk);
+    uint32_t* bufv = vals ? (uint32_t*)(ws + lay.bufv) : nullptr;
+    int64_t* rows = (int64_t*)(ws + lay.rows);
+    uint8_t* levels = (uint8_t*)(ws + lay.levels);
+    SegChunk* list = (SegChunk*)(ws + lay.list);
+    const int64_t stride = nseg + 1;
+    const int sms = num_sms_dev();
+    cudaError_t e = cudaMemsetAsync(ctl, 0, 256, s);
+    if (e != cudaSuccess) return e;
+    e = launch(K_SEG_PLAN, seg_count_kernel, dim3((unsigned)ceil_div(nseg, 256)), dim3(256), 0, s, off, nseg, lay.L,
+               sch.small_max, rows, levels, (const int*)ctl);
+    if (e != cudaSuccess) return e;
+    e = launch(K_SEG_PLAN, seg_scan_kernel, dim3((unsigned)(2 + lay.L)), dim3(1024), 0, s, rows, nseg,
+               (const int*)ctl);
+    if (e != cudaSuccess) return e;
+    if (sch.small_max > 0) {
+        if (sch.small_threads == 64)
+            e = launch(K_SEG_TILE, seg_tile_kernel<64, 16>, dim3((unsigned)(sms * 8)), dim3(64), sizeof(SmemKV<1024>),
+                       s, keys, vals, bufk, bufv, off, nseg, (const int64_t*)rows, (const uint8_t*)levels, mode,
+                       (const int*)ctl);
+        else
+            e = launch(K_SEG_TILE, seg_tile_kernel<128, 16>, dim3((unsigned)(sms * 8)), dim3(128),
+                       sizeof(SmemKV<2048>), s, keys, vals, bufk, bufv, off, nseg, (const int64_t*)rows,
+                       (const uint8_t*)levels, mode, (const int*)ctl);
+        if (e != cudaSuccess) return e;
+    }
+    e = launch(K_SEG_TILE, seg_tile_kernel<256, 16>, dim3((unsigned)(sms * 4)), dim3(256), sizeof(SmemKV<4096>), s,
+               keys, vals, bufk, bufv, off, nseg, (const int64_t*)(rows + stride), (const uint8_t*)levels, mode,
+               (const int*)ctl);
+    if (e != cudaSuccess) return e;
+    for (int p = 0; p < lay.L; ++p) {
+        const int64_t* prefix = rows + (2 + p) * stride;
+        e = launch(K_SEG_MERGE, seg_partition_kernel, dim3((unsigned)ceil_div(lay.max_items, 256)), dim3(256), 0, s,
+                   (const uint64_t*)keys, (const uint64_t*)bufk, off, nseg, prefix, (const uint8_t*)levels, p, list,
+                   (const int*)ctl);
+        if (e != cudaSuccess) return e;
+        const int64_t grid = lay.max_items < (int64_t)sms * TMA_CTAS_PER_SM ? lay.max_items
+                                                                             : (int64_t)sms * TMA_CTAS_PER_SM;
+        e = launch(K_SEG_MERGE, seg_merge_tma_kernel<TMA_THREADS, TMA_ITEMS>, dim3((unsigned)grid), dim3(TMA_THREADS),
+                   sizeof(MergeSmem<TMA_CHUNK>), s, keys, vals, bufk, bufv, (const SegChunk*)list,
+                   (const int64_t*)(prefix + nseg), mode, call_err, wait_limit_ns(), (const int*)ctl);
+        if (e != cudaSuccess) return e;
+    }
+    return publish_call_error(call_err, s);
+}
+
+// ---------------------------------------------------------------- tuning + graph cache
+struct TuneEntry {
+    int dev;
+    int64_t n, nseg;
+    const void* off;
+    int sched;
+};
+struct GraphEntry {
+    int dev;
+    void *keys, *vals;
+    const void* off;
+    int64_t n, nseg;
+    int mode, sched;
+    cudaGraphExec_t exec;
+    char* ws;
+    uint64_t kernels;    // kernel launches inside the graph
+};
+
+std::mutex g_seg_mu;
+std::vector<TuneEntry> g_tuned;
+std::vector<GraphEntry> g_graphs;       // small LRU (most recent last)
+constexpr size_t kMaxGraphs = 4;
+
+cudaStream_t capture_stream()
+{
+    static std::vector<cudaStream_t> streams;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if ((int)streams.size() <= dev) streams.resize(dev + 1, nullptr);
+    if (!streams[dev]) cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
+    return streams[dev];
+}
+
+// Times every candidate schedule on a scratch copy of the input and returns the
+// fastest (synchronises the stream).
+int autotune(uint64_t* keys, uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, int mode,
+             cudaStream_t s, int* rc)
+{
+    *rc = GNS_OK;
+    const SegLayout lay = seg_layout(n, nseg, vals != nullptr);
+    const size_t kb = align256((size_t)n * 8), vb = vals ? align256((size_t)n * 4) : 0;
+    char* ws = (char*)ws_alloc(lay.total + 2 * (kb + vb), s);
+    if (!ws) {
+        *rc = GNS_ERR_OOM;
+        return 0;
+    }
+    uint64_t* tk = (uint64_t*)(ws + lay.total);
+    uint32_t* tv = vals ? (uint32_t*)(ws + lay.total + kb) : nullptr;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 0;
+    float best_ms = 1e30f;
+    const int ncand = (int)(sizeof(kCandidates) / sizeof(kCandidates[0]));
+    for (int c = 0; c < ncand && *rc == GNS_OK; ++c) {
+        for (int rep = 0; rep < 2; ++rep) {   // first run warms up
+            if (cudaMemcpyAsync(tk, keys, (size_t)n * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+                (vals && cudaMemcpyAsync(tv, vals, (size_t)n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)) {
+                *rc = GNS_ERR_CUDA;
+                break;
+            }
+            cudaEventRecord(e0, s);
+            if (seg_enqueue(tk, tv, off, nseg, n, mode, kCandidates[c], ws, lay, s) != cudaSuccess) {
+                *rc = GNS_ERR_CUDA;
+                break;
+            }
+            cudaEventRecord(e1, s);
+        }
+        if (*rc != GNS_OK) break;
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ws_free(ws, s);
+    return best;
+}
+
+}  // namespace
+
+// Segmented sort entry (all checks done by the caller).
+int segmented_sort_device(uint64_t* keys, uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, int mode,
+                          cudaStream_t s)
+{
+    if (nseg == 0 || n <= 1) return GNS_OK;
+    seg_init_attributes();
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GNS_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_seg_mu);
+    // 1. the tuned schedule for this shape
+    int sched = -1;
+    for (auto& t : g_tuned)
+        if (t.dev == dev && t.n == n && t.nseg == nseg && t.off == off) sched = t.sched;
+    if (sched < 0) {
+        const char* fixed = getenv("GNS_SEG_SCHEDULE");
+        if (fixed) {
+            sched = atoi(fixed);
+            if (sched < 0 || sched > 2) sched = 0;
+        } else {
+            int rc = GNS_OK;
+            sched = autotune(keys, vals, off, nseg, n, mode, s, &rc);
+            if (rc != GNS_OK) return rc;
+        }
+        g_tuned.push_back({dev, n, nseg, (const void*)off, sched});
+    }
+    // 2. the captured graph for these pointers
+    for (size_t i = 0; i < g_graphs.size(); ++i) {
+        GraphEntry& g = g_graphs[i];
+        if (g.dev == dev && g.keys == keys && g.vals == vals && g.off == off && g.n == n && g.nseg == nseg &&
+            g.mode == mode && g.sched == sched) {
+            GraphEntry hit = g;
+            g_graphs.erase(g_graphs.begin() + i);
+            g_graphs.push_back(hit);
+            g_launches.fetch_add(hit.kernels, std::memory_order_relaxed);
+            return cudaGraphLaunch(hit.exec, s) == cudaSuccess ? GNS_OK : GNS_ERR_CUDA;
+        }
+    }
+    const SegLayout lay = seg_layout(n, nseg, vals != nullptr);
+    char* ws = (char*)ws_alloc(lay.total, s);
+    if (!ws) return GNS_ERR_OOM;
+    // the workspace must exist before the graph first runs
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        ws_free(ws, s);
+        return GNS_ERR_CUDA;
+    }
+    if (!status_word_ptr()) {   // resolve the status word before capturing
+        ws_free(ws, s);
+        return GNS_ERR_CUDA;
+    }
+    cudaStream_t cs = capture_stream();
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    set_capturing(true);
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e2 = seg_enqueue(keys, vals, off, nseg, n, mode, kCandidates[sched], ws, lay, cs);
+        e = cudaStreamEndCapture(cs, &graph);
+        if (e2 != cudaSuccess) e = e2;
+    }
+    const uint64_t kernels = take_captured_launches();
+    set_capturing(false);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ws_free(ws, s);
+        return GNS_ERR_CUDA;
+    }
+    if (g_graphs.size() >= kMaxGraphs) {
+        GraphEntry old = g_graphs.front();
+        g_graphs.erase(g_graphs.begin());
+        cudaStreamSynchronize(s);
+        cudaGraphExecDestroy(old.exec);
+        ws_free(old.ws, s);
+    }
+    g_graphs.push_back({dev, keys, vals, off, n, nseg, mode, sched, exec, ws, kernels});
+    g_launches.fetch_add(kernels, std::memory_order_relaxed);
+    return cudaGraphLaunch(exec, s) == cudaSuccess ? GNS_OK : GNS_ERR_CUDA;
+}
+
+size_t segmented_workspace_bytes(int64_t n, int64_t nseg) { return seg_layout(n, nseg, true).total; }
+
+int segmented_schedule_of(int64_t n, int64_t nseg, const void* off)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_seg_mu);
+    for (auto& t : g_tuned)
+        if (t.dev == dev && t.n == n && t.nseg == nseg && t.off == off) return t.sched;
+    return -1;
+}
+
+void segmented_release_graphs(cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lk(g_seg_mu);
+    cudaStreamSynchronize(s);
+    for (auto& g : g_graphs) {
+        cudaGraphExecDestroy(g.exec);
+        ws_free(g.ws, s);
+    }
+    g_graphs.clear();
+    g_tuned.clear();
+}
+
+}  // namespace gns
+
+using namespace gns;
 
 extern "C" {
-
-int gns_segmented_sort(int64_t* keys, uint32_t* payload, const int64_t* offsets, int64_t nseg,
-                       gns_stream_t stream)
-{
-    (void)keys; (void)payload; (void)offsets; (void)nseg; (void)stream;
-    return GNS_ERR_UNSUPPORTED;
-}
 
 int gns_segmented_sort_ex(void* keys, int key_type, uint32_t* payload, const int64_t* offsets, int64_t nseg,
                           int64_t total_n, int order, gns_stream_t stream)
 {
-    (void)keys; (void)key_type; (void)payload; (void)offsets; (void)nseg; (void)total_n; (void)order;
-    (void)stream;
-    return GNS_ERR_UNSUPPORTED;
+    if (nseg < 0 || total_n < 0) return GNS_ERR_INVALID;
+    if (key_type != GNS_KEY_F64 && key_type != GNS_KEY_I64) return GNS_ERR_INVALID;
+    if (order != GNS_ASCENDING && order != GNS_DESCENDING) return GNS_ERR_INVALID;
+    if (nseg > 0 && offsets == nullptr) return GNS_ERR_INVALID;
+    if (total_n > 0 && keys == nullptr) return GNS_ERR_INVALID;
+    if (((uintptr_t)keys & 7) || ((uintptr_t)payload & 3) || ((uintptr_t)offsets & 7)) return GNS_ERR_INVALID;
+    if (nseg > 0x7fffffff) return GNS_ERR_UNSUPPORTED;
+    const int mode = (key_type == GNS_KEY_I64 ? MODE_I64 : 0) | (order == GNS_DESCENDING ? MODE_DESC : 0);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = segmented_sort_device((uint64_t*)keys, payload, offsets, nseg, total_n, mode, s);
+    return finish_call(rc, s);
 }
+
+int gns_segmented_sort(int64_t* keys, uint32_t* payload, const int64_t* offsets, int64_t nseg, gns_stream_t stream)
+{
+    if (nseg < 0) return GNS_ERR_INVALID;
+    if (nseg == 0) return GNS_OK;
+    if (offsets == nullptr) return GNS_ERR_INVALID;
+    int64_t total = 0;
+    // the host needs the total length to size the workspace: one 8-byte read
+    if (cudaMemcpyAsync(&total, offsets + nseg, sizeof(int64_t), cudaMemcpyDeviceToHost, (cudaStream_t)stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+        return GNS_ERR_CUDA;
+    return gns_segmented_sort_ex(keys, GNS_KEY_I64, payload, offsets, nseg, total, GNS_ASCENDING, stream);
+}
+
+int gns_segmented_schedule(int64_t total_n, int64_t nseg, const int64_t* offsets)
+{
+    return segmented_schedule_of(total_n, nseg, offsets);
+}
+
+void gns_segmented_release(gns_stream_t stream) { segmented_release_graphs((cudaStream_t)stream); }
 
 }  // extern "C"

@@ -100,3 +100,15 @@ def test_workspace_bytes_match_tiers(L):
     assert 1.5 <= ram_half < 1.51
     assert L.gns_workspace_bytes(1, 1.0, 0) == 0
     assert L.gns_workspace_bytes(4096, 1.0, 0) <= 4096
+
+
+def test_segmented_host_argument_checks(L):
+    # nseg < 0, bad key type, bad order, NULL offsets with segments, misaligned offsets
+    assert L.gns_segmented_sort_ex(FAKE, 1, None, FAKE, -1, 10, 0, None) == -1
+    assert L.gns_segmented_sort_ex(FAKE, 7, None, FAKE, 1, 10, 0, None) == -1
+    assert L.gns_segmented_sort_ex(FAKE, 1, None, FAKE, 1, 10, 3, None) == -1
+    assert L.gns_segmented_sort_ex(FAKE, 1, None, None, 1, 10, 0, None) == -1
+    assert L.gns_segmented_sort_ex(FAKE, 1, None, FAKE + 4, 1, 10, 0, None) == -1
+    assert L.gns_segmented_sort_ex(FAKE, 1, None, FAKE, 0, 0, 0, None) == 0     # nothing to sort
+    assert L.gns_segmented_sort(FAKE, None, FAKE, -2, None) == -1
+    assert L.gns_segmented_sort(FAKE, None, FAKE, 0, None) == 0
