@@ -1,0 +1,87 @@
+"""Oracle for the learned-splitter path -- TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+The paper has no learned component; this restates, in float64 NumPy, what the
+library's learned path computes, so that the GPU kernels can be compared with
+it step by step:
+
+* the network: 1 input, two tanh layers of 32 units, one sigmoid output;
+  parameters packed as [w1(32), b1(32), W2(32x32, row j = inputs of unit j),
+  b2(32), w3(32), b3(1)] -- 1153 numbers;
+* the loss: mean squared error to a target CDF value;
+* its gradient (backpropagation written out by hand) -- pinned in the tests
+  by central finite differences of the loss, which share no code with it;
+* one Adam step;
+* the normalisation of a key to the network input and the integer bucket
+  function defined by a splitter array (53-bit prefixes of the order map).
+
+The final result of the learned sort is the plain stable sort, so it is
+checked against ``oracle.stable_sort``, not against anything here.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+H = 32
+NPARAM = H + H + H * H + H + H + 1
+W1, B1, W2, B2, W3, B3 = 0, H, 2 * H, 2 * H + H * H, 3 * H + H * H, 4 * H + H * H
+
+
+def unpack(p):
+    p = np.asarray(p, dtype=np.float64)
+    return (p[W1:B1], p[B1:W2], p[W2:B2].reshape(H, H), p[B2:W3], p[W3:B3], p[B3])
+
+
+def forward(p, x):
+    """y = sigmoid(w3 . tanh(W2 tanh(w1 x + b1) + b2) + b3) for every x."""
+    w1, b1, w2, b2, w3, b3 = unpack(p)
+    x = np.asarray(x, dtype=np.float64)
+    h1 = np.tanh(np.outer(x, w1) + b1)            # (m, H)
+    h2 = np.tanh(h1 @ w2.T + b2)                  # (m, H)
+    z3 = h2 @ w3 + b3                             # (m,)
+    y = 1.0 / (1.0 + np.exp(-z3))
+    return y, (x, h1, h2)
+
+
+def loss(p, x, t):
+    y, _ = forward(p, x)
+    return float(np.mean((y - np.asarray(t, dtype=np.float64)) ** 2))
+
+
+def loss_grad(p, x, t):
+    """Mean squared error and its gradient with respect to the packed params."""
+    w1, b1, w2, b2, w3, b3 = unpack(p)
+    y, (x, h1, h2) = forward(p, x)
+    t = np.asarray(t, dtype=np.float64)
+    m = x.size
+    dy = 2.0 * (y - t) / m                       # dL/dy
+    dz3 = dy * y * (1.0 - y)                     # sigmoid'
+    g_w3 = h2.T @ dz3
+    g_b3 = dz3.sum()
+    dz2 = np.outer(dz3, w3) * (1.0 - h2 ** 2)    # (m, H)
+    g_w2 = dz2.T @ h1                            # row j, column i
+    g_b2 = dz2.sum(axis=0)
+    dz1 = (dz2 @ w2) * (1.0 - h1 ** 2)           # (m, H)
+    g_w1 = dz1.T @ x
+    g_b1 = dz1.sum(axis=0)
+    g = np.concatenate([g_w1, g_b1, g_w2.ravel(), g_b2, g_w3, [g_b3]])
+    return float(np.mean((y - t) ** 2)), g
+
+
+def adam_step(p, g, m1, m2, step, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba), step counted from 1.  Returns new p, m1, m2."""
+    m1 = beta1 * m1 + (1 - beta1) * g
+    m2 = beta2 * m2 + (1 - beta2) * g * g
+    mh = m1 / (1 - beta1 ** step)
+    vh = m2 / (1 - beta2 ** step)
+    return p - lr * mh / (np.sqrt(vh) + eps), m1, m2
+
+
+def key53(keys_bits_encoded):
+    """53-bit prefix of order-mapped keys (the unit the bucket function works in)."""
+    return np.asarray(keys_bits_encoded, dtype=np.uint64) >> np.uint64(11)
+
+
+def buckets_from_splitters(e53, spl53):
+    """Bucket of each key: the number of splitters at or below it (monotone, so
+    equal keys always share a bucket)."""
+    return np.searchsorted(np.asarray(spl53, dtype=np.uint64), np.asarray(e53, dtype=np.uint64), side="right")
