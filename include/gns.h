@@ -182,6 +182,76 @@ int gns_sort_noalloc(double* keys, uint32_t* payload, int64_t n, int order,
 int gns_segmented_schedule(int64_t total_n, int64_t nseg, const int64_t* offsets);
 void gns_segmented_release(gns_stream_t stream);
 
+/*
+ * Learned-splitter sort (no counterpart in the paper; a training-system
+ * pattern applied to the same stable sort, which it must reproduce exactly).
+ *
+ * gns_learned_sort sorts float64 keys like gns_sort at the 100% tier, in three
+ * phases:
+ *   1. fit: 2^16 keys sampled at even strides are sorted; an FP32 MLP
+ *      (1 -> 32 tanh -> 32 tanh -> 1 sigmoid) is trained on the device to the
+ *      sample's empirical CDF, as a function of the 53-bit prefix of the
+ *      order-mapped key normalised to [0, 1] (Adam, mean squared error).
+ *   2. partition: the network, evaluated on a 2^16-point grid and made monotone
+ *      by a running maximum, proposes 4095 splitters (its inverse at j/4096).
+ *      A key's bucket is the number of splitters at or below its 53-bit prefix
+ *      -- an integer, monotone function of the key, so equal keys share a
+ *      bucket and the concatenation of stably sorted buckets is exactly the
+ *      stable sort, however good or bad the network is.  The 4096-way stable
+ *      partition is two 64-way stable scatter passes (low, then high 6 bits of
+ *      the bucket).
+ *   3. bucket sort: every bucket is a segment for the segmented sort; a bucket
+ *      that came out larger than `overfull_factor` times the mean is simply
+ *      sorted by more merge levels of the same merge path (the plain merge
+ *      path is the fallback for it), and if the splitters were not
+ *      non-decreasing, or buffer_fraction < 1, or n < 2^20, the whole call
+ *      falls back to gns_sort.
+ * params: NULL = defaults.  report: if not NULL, the call synchronises the
+ * stream and fills it.
+ */
+typedef struct {
+    int train_steps;         /* Adam steps (default 256); 0 = no network:
+                                splitters evenly spaced in the normalised key
+                                space (the method without the learned part)  */
+    int batch;               /* samples per step, multiple of 512 (default 1024) */
+    float learning_rate;     /* default 1e-2                                  */
+    float overfull_factor;   /* bucket counted overfull above this x mean (4) */
+} gns_learned_params;
+
+typedef struct {
+    int fallback;            /* 1: the call ran gns_sort instead               */
+    int nonempty_buckets;
+    int64_t max_bucket;      /* largest bucket (keys)                          */
+    int overfull_buckets;
+    float final_loss;        /* training loss of the last step                 */
+    float fit_ms, partition_ms, bucket_sort_ms;   /* per-phase device time     */
+} gns_learned_report;
+
+int gns_learned_sort(double* keys, uint32_t* payload, int64_t n, int order, double buffer_fraction,
+                     const gns_learned_params* params, gns_learned_report* report, gns_stream_t stream);
+
+/*
+ * The network's own kernels, exposed for gradient checks (device pointers;
+ * params packed as [w1(32), b1(32), W2(32x32 row-major: row j holds the
+ * inputs of unit j of layer 2), b2(32), w3(32), b3], 1153 floats).
+ *   gns_mlp_forward:   y[i] = net(x[i]).
+ *   gns_mlp_loss_grad: loss = mean_i (net(x[i]) - t[i])^2 and its gradient
+ *                      with respect to the packed params (1153 floats).
+ *   gns_mlp_train:     `steps` Adam steps from params_in on (x, t) (m a power
+ *                      of two), batch b at step s = samples
+ *                      ((s*batch + i) * 40503) mod m, i < batch; writes
+ *                      params_out and the last step's loss.
+ * Return GNS_OK, GNS_ERR_INVALID or GNS_ERR_CUDA.
+ */
+int gns_mlp_forward(const float* params, const float* x, int64_t m, float* y, gns_stream_t stream);
+int gns_mlp_loss_grad(const float* params, const float* x, const float* t, int64_t m, float* grad,
+                      float* loss, gns_stream_t stream);
+int gns_mlp_train(const float* x, const float* t, int64_t m, const float* params_in, float* params_out,
+                  float* loss_out, int steps, int batch, float learning_rate, gns_stream_t stream);
+
+/* The initial network of the learned sort (1153 floats, host memory). */
+void gns_mlp_init_params(float* params_host);
+
 /* Size in bytes of the scratch a call allocates.  kind = GNS_WS_SORT for
  * gns_sort at this buffer_fraction, GNS_WS_LEARNED for gns_learned_sort. */
 size_t gns_workspace_bytes(int64_t n, double buffer_fraction, int kind);

@@ -48,6 +48,11 @@ def lib() -> ctypes.CDLL:
                 "gns_sort_i64": ([P, P, i64, i32, f64, P], i32),
                 "gns_sort_host": ([P, P, i64, i32, i32, f64, P], i32),
                 "gns_sort_noalloc": ([P, P, i64, i32, P], i32),
+                "gns_learned_sort": ([P, P, i64, i32, f64, P, P, P], i32),
+                "gns_mlp_forward": ([P, P, i64, P, P], i32),
+                "gns_mlp_loss_grad": ([P, P, P, i64, P, P, P], i32),
+                "gns_mlp_train": ([P, P, i64, P, P, P, i32, i32, ctypes.c_float, P], i32),
+                "gns_mlp_init_params": ([P], None),
                 "gns_segmented_sort": ([P, P, P, i64, P], i32),
                 "gns_segmented_sort_ex": ([P, i32, P, P, i64, i64, i32, P], i32),
                 "gns_workspace_bytes": ([i64, f64, i32], ctypes.c_size_t),
@@ -152,6 +157,72 @@ def gns_sort_noalloc(keys, payload=None, order: int = ASCENDING, stream=None) ->
         raise ValueError("payload must have as many elements as keys")
     _check(lib().gns_sort_noalloc(_dev_ptr(keys, torch.float64, "keys"), _dev_ptr(payload, torch.int32, "payload"),
                                   n, order, _stream(stream)), "gns_sort_noalloc")
+
+
+class LearnedParams(ctypes.Structure):
+    _fields_ = [("train_steps", ctypes.c_int), ("batch", ctypes.c_int), ("learning_rate", ctypes.c_float),
+                ("overfull_factor", ctypes.c_float)]
+
+
+class LearnedReport(ctypes.Structure):
+    _fields_ = [("fallback", ctypes.c_int), ("nonempty_buckets", ctypes.c_int), ("max_bucket", ctypes.c_int64),
+                ("overfull_buckets", ctypes.c_int), ("final_loss", ctypes.c_float), ("fit_ms", ctypes.c_float),
+                ("partition_ms", ctypes.c_float), ("bucket_sort_ms", ctypes.c_float)]
+
+
+def gns_learned_sort(keys, payload=None, order: int = ASCENDING, buffer_fraction: float = 1.0,
+                     train_steps: int = 256, batch: int = 1024, learning_rate: float = 1e-2,
+                     overfull_factor: float = 4.0, report: bool = False, stream=None):
+    """Learned-splitter stable sort of a CUDA float64 tensor; with report=True the
+    call synchronises and returns the report as a dict."""
+    import torch
+    n = keys.numel()
+    if payload is not None and payload.numel() != n:
+        raise ValueError("payload must have as many elements as keys")
+    prm = LearnedParams(train_steps, batch, learning_rate, overfull_factor)
+    rep = LearnedReport() if report else None
+    _check(lib().gns_learned_sort(_dev_ptr(keys, torch.float64, "keys"), _dev_ptr(payload, torch.int32, "payload"),
+                                  n, order, float(buffer_fraction), ctypes.byref(prm),
+                                  ctypes.byref(rep) if rep is not None else None, _stream(stream)),
+           "gns_learned_sort")
+    if rep is None:
+        return None
+    return {name: getattr(rep, name) for name, _ in LearnedReport._fields_}
+
+
+def gns_mlp_init_params():
+    out = np.zeros(1153, dtype=np.float32)
+    lib().gns_mlp_init_params(ctypes.c_void_p(out.ctypes.data))
+    return out
+
+
+def gns_mlp_forward(params, x, stream=None):
+    import torch
+    y = torch.empty_like(x)
+    _check(lib().gns_mlp_forward(_dev_ptr(params, torch.float32, "params"), _dev_ptr(x, torch.float32, "x"),
+                                 x.numel(), _dev_ptr(y, torch.float32, "y"), _stream(stream)), "gns_mlp_forward")
+    return y
+
+
+def gns_mlp_loss_grad(params, x, t, stream=None):
+    import torch
+    grad = torch.empty(1153, dtype=torch.float32, device=x.device)
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    _check(lib().gns_mlp_loss_grad(_dev_ptr(params, torch.float32, "params"), _dev_ptr(x, torch.float32, "x"),
+                                   _dev_ptr(t, torch.float32, "t"), x.numel(), _dev_ptr(grad, torch.float32, "grad"),
+                                   _dev_ptr(loss, torch.float32, "loss"), _stream(stream)), "gns_mlp_loss_grad")
+    return loss, grad
+
+
+def gns_mlp_train(x, t, params, steps: int, batch: int = 1024, learning_rate: float = 1e-2, stream=None):
+    import torch
+    out = torch.empty(1153, dtype=torch.float32, device=x.device)
+    loss = torch.zeros(1, dtype=torch.float32, device=x.device)
+    _check(lib().gns_mlp_train(_dev_ptr(x, torch.float32, "x"), _dev_ptr(t, torch.float32, "t"), x.numel(),
+                               _dev_ptr(params, torch.float32, "params"), _dev_ptr(out, torch.float32, "out"),
+                               _dev_ptr(loss, torch.float32, "loss"), steps, batch, float(learning_rate),
+                               _stream(stream)), "gns_mlp_train")
+    return out, loss
 
 
 def gns_segmented_sort(keys, payload, offsets, order: int = ASCENDING, stream=None) -> None:

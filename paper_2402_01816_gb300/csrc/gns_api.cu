@@ -285,6 +285,10 @@ size_t gns_workspace_bytes(int64_t n, double buffer_fraction, int kind)
 {
     if (n < 0 || isnan(buffer_fraction)) return 0;
     if (kind == GNS_WS_SORT) return sort_workspace_bytes(n, buffer_fraction);
+    if (kind == GNS_WS_LEARNED) {
+        if (buffer_fraction < 1.0 || n < (1ll << 20)) return sort_workspace_bytes(n, buffer_fraction);
+        return learned_workspace_bytes(n);
+    }
     return 0;
 }
 

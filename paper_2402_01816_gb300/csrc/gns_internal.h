@@ -93,5 +93,8 @@ size_t sort_workspace_bytes(int64_t n, double buffer_fraction);
 int segmented_sort_device(uint64_t* keys, uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, int mode,
                           cudaStream_t s);
 size_t segmented_workspace_bytes(int64_t n, int64_t nseg);
+int segmented_sort_direct(uint64_t* keys, uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, int mode,
+                          cudaStream_t s);
+size_t learned_workspace_bytes(int64_t n);
 
 }  // namespace gns

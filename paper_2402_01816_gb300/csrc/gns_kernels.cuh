@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(THREADS)
 {
     constexpr int T = THREADS * ITEMS;
     if (skip_all(presorted)) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     SmemKV<T>& sm = *reinterpret_cast<SmemKV<T>*>(smem_raw);
     const int t = threadIdx.x;
     const int64_t base = (int64_t)blockIdx.x * T;
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(THREADS)
 {
     constexpr int T = THREADS * ITEMS;
     if (skip_all(presorted)) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     SmemKV<T>& sm = *reinterpret_cast<SmemKV<T>*>(smem_raw);
     __shared__ int64_t s_leaf;
     __shared__ int s_ok;

@@ -1,0 +1,963 @@
+// gns_learned.cu -- the learned-splitter stable sort (no counterpart in the
+// paper) and the MLP kernels it trains with.
+//
+// Exactness does not depend on the network: a key's bucket is an integer,
+// monotone function of its order-mapped 53-bit prefix (the number of splitters
+// at or below it), so equal keys share a bucket and stably sorting every bucket
+// after a stable partition gives exactly the stable sort.  The network only
+// decides where the 4095 splitters go.
+#include <cooperative_groups.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "gns_internal.h"
+#include "gns_kernels.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace gns {
+
+namespace {
+
+// ---------------------------------------------------------------- the network
+constexpr int MH = 32;                              // hidden units per layer
+constexpr int NP = MH + MH + MH * MH + MH + MH + 1; // 1153 parameters
+constexpr int P_W1 = 0, P_B1 = 32, P_W2 = 64, P_B2 = 64 + 1024, P_W3 = P_B2 + 32, P_B3 = P_W3 + 32;
+constexpr unsigned FULL = 0xffffffffu;
+
+constexpr int SAMPLE_M = 1 << 16;     // sample size (power of two)
+constexpr int GRID_G = 1 << 16;       // grid for inverting the fitted CDF
+constexpr int NBUCKETS = 4096;
+constexpr int NSPLIT = NBUCKETS - 1;
+constexpr int TABLE_BITS = 13;        // bins of the key -> bucket-range table
+constexpr int PART_TILE = 2048;       // keys per partition tile
+constexpr int PART_THREADS = 256;
+constexpr int PART_ITEMS = PART_TILE / PART_THREADS;
+constexpr int FIT_CTAS = 8;           // cluster size of the trainer
+constexpr int FIT_THREADS = 256;
+
+// Parameters in shared memory: the packed vector (W2 row-major) plus W2
+// transposed, so that both the forward pass (lane j walks row j) and the
+// backward pass (lane i walks column i) read consecutive words per step.
+struct NetSmem {
+    float p[NP];
+    float w2t[MH * MH];
+};
+
+__device__ __forceinline__ void load_net(NetSmem& s, const float* __restrict__ params)
+{
+    for (int i = threadIdx.x; i < NP; i += blockDim.x) s.p[i] = params[i];
+    __syncthreads();
+    for (int k = threadIdx.x; k < MH * MH; k += blockDim.x) {
+        const int j = k / MH, i = k % MH;
+        s.w2t[i * MH + j] = s.p[P_W2 + k];
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int d = 16; d; d >>= 1) v += __shfl_xor_sync(FULL, v, d);
+    return v;
+}
+
+// Forward pass of one sample by one warp, lane j = hidden unit j.  Returns y
+// in every lane; keeps this lane's activations and all of layer 1.
+__device__ __forceinline__ float net_forward(const NetSmem& s, float x, float& h1j, float& h2j, float (&h1)[MH])
+{
+    const int j = threadIdx.x & 31;
+    h1j = tanhf(fmaf(s.p[P_W1 + j], x, s.p[P_B1 + j]));
+    float z = s.p[P_B2 + j];
+#pragma unroll
+    for (int i = 0; i < MH; ++i) {
+        h1[i] = __shfl_sync(FULL, h1j, i);
+        z = fmaf(s.w2t[i * MH + j], h1[i], z);
+    }
+    h2j = tanhf(z);
+    const float z3 = warp_sum(s.p[P_W3 + j] * h2j) + s.p[P_B3];
+    return 1.0f / (1.0f + expf(-z3));
+}
+
+// Per-lane gradient accumulators: lane j holds unit j's entries; dw2[i] is
+// d/dW2[j][i].  b3 and the loss are the same in every lane.
+struct NetGrad {
+    float w1, b1, b2, w3, b3, loss;
+    float dw2[MH];
+};
+
+__device__ __forceinline__ void grad_zero(NetGrad& g)
+{
+    g.w1 = g.b1 = g.b2 = g.w3 = g.b3 = g.loss = 0.f;
+#pragma unroll
+    for (int i = 0; i < MH; ++i) g.dw2[i] = 0.f;
+}
+
+// Backward pass of (y - t)^2 * scale for one sample (scale = 1 / batch size).
+__device__ __forceinline__ void net_backward(const NetSmem& s, float x, float t, float y, float h1j, float h2j,
+                                             const float (&h1)[MH], float scale, NetGrad& g)
+{
+    const int j = threadIdx.x & 31;
+    const float e = y - t;
+    g.loss += e * e * scale;
+    const float dz3 = 2.0f * e * scale * y * (1.0f - y);
+    g.w3 = fmaf(dz3, h2j, g.w3);
+    g.b3 += dz3;
+    const float dz2 = dz3 * s.p[P_W3 + j] * (1.0f - h2j * h2j);
+    g.b2 += dz2;
+#pragma unroll
+    for (int i = 0; i < MH; ++i) g.dw2[i] = fmaf(dz2, h1[i], g.dw2[i]);
+    float dh1 = 0.f;   // this lane as layer-1 unit j: sum over layer-2 units jj
+#pragma unroll
+    for (int jj = 0; jj < MH; ++jj) dh1 = fmaf(s.p[P_W2 + jj * MH + j], __shfl_sync(FULL, dz2, jj), dh1);
+    const float dz1 = dh1 * (1.0f - h1j * h1j);
+    g.w1 = fmaf(dz1, x, g.w1);
+    g.b1 += dz1;
+}
+
+// Writes a warp's gradient into row `out` (NP + 1 floats, the last the loss),
+// with the W2 block transposed (column-major) so that the writes are
+// consecutive across lanes.
+__device__ __forceinline__ void grad_store_t(const NetGrad& g, float* out)
+{
+    const int j = threadIdx.x & 31;
+    out[P_W1 + j] = g.w1;
+    out[P_B1 + j] = g.b1;
+    out[P_B2 + j] = g.b2;
+    out[P_W3 + j] = g.w3;
+#pragma unroll
+    for (int i = 0; i < MH; ++i) out[P_W2 + i * MH + j] = g.dw2[i];
+    if (j == 0) {
+        out[P_B3] = g.b3;
+        out[NP] = g.loss;
+    }
+}
+
+// Index in the packed (row-major) vector of entry q of a transposed gradient row.
+__device__ __forceinline__ int packed_index(int q)
+{
+    if (q < P_W2 || q >= P_B2) return q;
+    const int k = q - P_W2, i = k / MH, j = k % MH;
+    return P_W2 + j * MH + i;
+}
+
+// ---------------------------------------------------------------- test kernels
+__global__ void __launch_bounds__(256) mlp_forward_kernel(const float* __restrict__ params, const float* __restrict__ x,
+                                                          int64_t m, float* __restrict__ y)
+{
+    __shared__ NetSmem s;
+    load_net(s, params);
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    for (int64_t i = gw; i < m; i += warps) {
+        float h1j, h2j, h1[MH];
+        const float yy = net_forward(s, x[i], h1j, h2j, h1);
+        if ((threadIdx.x & 31) == 0) y[i] = yy;
+    }
+}
+
+// One CTA: mean loss and gradient over all m samples (same device functions as
+// the trainer).
+__global__ void __launch_bounds__(256) mlp_loss_grad_kernel(const float* __restrict__ params,
+                                                            const float* __restrict__ x,
+                                                            const float* __restrict__ t, int64_t m,
+                                                            float* __restrict__ grad, float* __restrict__ loss)
+{
+    __shared__ NetSmem s;
+    __shared__ float gw[8][NP + 1];
+    load_net(s, params);
+    const int w = threadIdx.x / 32;
+    NetGrad g;
+    grad_zero(g);
+    const float scale = 1.0f / (float)m;
+    for (int64_t i = w; i < m; i += 8) {
+        float h1j, h2j, h1[MH];
+        const float xi = x[i];
+        const float yy = net_forward(s, xi, h1j, h2j, h1);
+        net_backward(s, xi, t[i], yy, h1j, h2j, h1, scale, g);
+    }
+    grad_store_t(g, gw[w]);
+    __syncthreads();
+    for (int q = threadIdx.x; q <= NP; q += blockDim.x) {
+        float acc = 0.f;
+        for (int k = 0; k < 8; ++k) acc += gw[k][q];
+        if (q == NP) *loss = acc;
+        else grad[packed_index(q)] = acc;
+    }
+}
+
+// ---------------------------------------------------------------- the trainer
+// A cluster of FIT_CTAS CTAs runs all Adam steps in one launch.  Every warp
+// takes batch/64 samples of the step, gradients are summed in each CTA, then
+// across the cluster through distributed shared memory (every CTA adds the
+// partial sums of all ranks in the same order, so all CTAs hold identical
+// parameters), and every CTA applies the same Adam update.
+struct FitSmem {
+    NetSmem net;
+    float m1[NP], m2[NP];
+    float gwarp[FIT_THREADS / 32][NP + 1];
+    float gcta[NP + 1];
+};
+
+__global__ void __cluster_dims__(FIT_CTAS, 1, 1) __launch_bounds__(FIT_THREADS)
+    mlp_train_kernel(const float* __restrict__ x, const float* __restrict__ t, int64_t m,
+                     const float* __restrict__ params_in, float* __restrict__ params_out, float* __restrict__ loss_out,
+                     int steps, int batch, float lr)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    FitSmem& s = *reinterpret_cast<FitSmem*>(smem_raw);
+    cg::cluster_group cluster = cg::this_cluster();
+    const unsigned rank = cluster.block_rank();
+    load_net(s.net, params_in);
+    for (int q = threadIdx.x; q < NP; q += blockDim.x) s.m1[q] = s.m2[q] = 0.f;
+    const int w = threadIdx.x / 32;
+    const int gwarp = (int)rank * (FIT_THREADS / 32) + w;
+    const int per_warp = batch / (FIT_CTAS * FIT_THREADS / 32);
+    const float scale = 1.0f / (float)batch;
+    const uint64_t mask = (uint64_t)m - 1;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    float last_loss = 0.f;
+    __syncthreads();
+    for (int step = 0; step < steps; ++step) {
+        NetGrad g;
+        grad_zero(g);
+        for (int k = 0; k < per_warp; ++k) {
+            const uint64_t slot = (uint64_t)step * (uint64_t)batch + (uint64_t)(gwarp * per_warp + k);
+            const uint64_t idx = (slot * 40503ull) & mask;
+            float h1j, h2j, h1[MH];
+            const float xi = x[idx];
+            const float yy = net_forward(s.net, xi, h1j, h2j, h1);
+            net_backward(s.net, xi, t[idx], yy, h1j, h2j, h1, scale, g);
+        }
+        grad_store_t(g, s.gwarp[w]);
+        __syncthreads();
+        for (int q = threadIdx.x; q <= NP; q += blockDim.x) {
+            float acc = 0.f;
+            for (int k = 0; k < FIT_THREADS / 32; ++k) acc += s.gwarp[k][q];
+            s.gcta[q] = acc;
+        }
+        cluster.sync();                               // every rank's partial sums are ready
+        const float c1 = 1.0f - powf(b1, (float)(step + 1));
+        const float c2 = 1.0f - powf(b2, (float)(step + 1));
+        for (int q = threadIdx.x; q <= NP; q += blockDim.x) {
+            float acc = 0.f;
+            for (unsigned r = 0; r < FIT_CTAS; ++r) acc += cluster.map_shared_rank(s.gcta, r)[q];
+            if (q == NP) {
+                last_loss = acc;
+                continue;
+            }
+            const float mm = b1 * s.m1[q] + (1.0f - b1) * acc;
+            const float vv = b2 * s.m2[q] + (1.0f - b2) * acc * acc;
+            s.m1[q] = mm;
+            s.m2[q] = vv;
+            const float upd = lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+            const int pi = packed_index(q);
+            const float nv = s.net.p[pi] - upd;
+            s.net.p[pi] = nv;
+            if (q >= P_W2 && q < P_B2) s.net.w2t[q - P_W2] = nv;
+        }
+        cluster.sync();                               // remote reads done; parameters updated
+    }
+    if (rank == 0) {
+        for (int q = threadIdx.x; q < NP; q += blockDim.x) params_out[q] = s.net.p[q];
+        if (threadIdx.x == (NP % blockDim.x) && loss_out) *loss_out = last_loss;
+    }
+}
+
+// ---------------------------------------------------------------- splitters
+struct LearnMeta {
+    uint64_t lo53;        // 53-bit prefix of the smallest sample key
+    uint64_t range;       // prefix of the largest minus lo53 (>= 1)
+    int sh;               // table bin = (prefix - lo53) >> sh
+    int bad;              // splitters not non-decreasing (never expected)
+    int64_t max_bucket;
+    int nonempty, overfull;
+};
+
+__global__ void sample_kernel(const uint64_t* __restrict__ keys, int64_t n, uint64_t* __restrict__ sample)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < SAMPLE_M) sample[i] = keys[(i * n) / SAMPLE_M];
+}
+
+// Normalised inputs and targets of the sorted sample; meta range.
+__global__ void fit_inputs_kernel(const uint64_t* __restrict__ sample, int mode, float* __restrict__ x,
+                                  float* __restrict__ t, LearnMeta* meta)
+{
+    const uint64_t lo = encode_key(sample[0], mode) >> 11;
+    const uint64_t hi = encode_key(sample[SAMPLE_M - 1], mode) >> 11;
+    const uint64_t range = hi > lo ? hi - lo : 1;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        meta->lo53 = lo;
+        meta->range = range;
+        int sh = 0;
+        while ((range >> sh) >= (1ull << TABLE_BITS)) ++sh;
+        meta->sh = sh;
+        meta->bad = 0;
+    }
+    if (i < SAMPLE_M) {
+        const uint64_t e = encode_key(sample[i], mode) >> 11;
+        const double d = (double)(e > lo ? e - lo : 0) / (double)range;
+        x[i] = (float)(d < 1.0 ? d : 1.0);
+        t[i] = ((float)i + 0.5f) / (float)SAMPLE_M;
+    }
+}
+
+// F[g] = net(g / (G - 1)); without a network (params == nullptr) F[g] = g / (G - 1):
+// splitters evenly spaced in the normalised key space.
+__global__ void __launch_bounds__(256) grid_eval_kernel(const float* __restrict__ params, float* __restrict__ F)
+{
+    __shared__ NetSmem s;
+    if (params == nullptr) {
+        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < GRID_G; g += gridDim.x * blockDim.x)
+            F[g] = (float)g / (float)(GRID_G - 1);
+        return;
+    }
+    load_net(s, params);
+    const int warps = gridDim.x * (blockDim.x / 32);
+    const int gw = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    for (int g = gw; g < GRID_G; g += warps) {
+        float h1j, h2j, h1[MH];
+        const float y = net_forward(s, (float)g / (float)(GRID_G - 1), h1j, h2j, h1);
+        if ((threadIdx.x & 31) == 0) F[g] = y;
+    }
+}
+
+// Running maximum over F (one CTA): the fitted CDF made non-decreasing.
+__global__ void __launch_bounds__(1024) running_max_kernel(float* F)
+{
+    __shared__ float tmax[1024];
+    constexpr int PER = GRID_G / 1024;
+    const int t = threadIdx.x;
+    float m = -1.0f;
+    for (int k = 0; k < PER; ++k) m = fmaxf(m, F[t * PER + k]);
+    tmax[t] = m;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {          // inclusive max-scan (Hillis-Steele)
+        float v = t >= d ? tmax[t - d] : -1.0f;
+        __syncthreads();
+        tmax[t] = fmaxf(tmax[t], v);
+        __syncthreads();
+    }
+    float run = t > 0 ? tmax[t - 1] : -1.0f;
+    for (int k = 0; k < PER; ++k) {
+        run = fmaxf(run, F[t * PER + k]);
+        F[t * PER + k] = run;
+    }
+}
+
+// Splitter j (1..4095): the prefix of the first grid point where the monotone
+// CDF reaches j / 4096.
+__global__ void splitter_kernel(const float* __restrict__ F, LearnMeta* meta, uint64_t* __restrict__ spl)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    if (j > NSPLIT) return;
+    const float q = (float)j / (float)NBUCKETS;
+    int lo = 0, hi = GRID_G - 1;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (F[mid] >= q) hi = mid;
+        else lo = mid + 1;
+    }
+    const uint64_t range = meta->range;
+    uint64_t off = (uint64_t)ceil((double)lo / (double)(GRID_G - 1) * (double)range);
+    if (off > range) off = range;
+    spl[j - 1] = meta->lo53 + off;
+}
+
+__device__ __forceinline__ int count_le(const uint64_t* spl, uint64_t e53)
+{
+    int lo = 0, hi = NSPLIT;                      // number of splitters <= e53
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (spl[mid] <= e53) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Table bin b -> [bucket of its first prefix, bucket of its last prefix]; also
+// checks that the splitters are non-decreasing.
+__global__ void table_kernel(const uint64_t* __restrict__ spl, LearnMeta* meta, uint32_t* __restrict__ table)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (1 << TABLE_BITS)) return;
+    const uint64_t lo53 = meta->lo53, range = meta->range;
+    const int sh = meta->sh;
+    const uint64_t dlo = (uint64_t)b << sh;
+    uint32_t entry;
+    if (dlo > range) {
+        entry = (uint32_t)NSPLIT | ((uint32_t)NSPLIT << 16);
+    } else {
+        uint64_t dhi = (((uint64_t)b + 1) << sh) - 1;
+        if (dhi > range) dhi = range;
+        entry = (uint32_t)count_le(spl, lo53 + dlo) | ((uint32_t)count_le(spl, lo53 + dhi) << 16);
+    }
+    table[b] = entry;
+    if (b > 0 && b < NSPLIT && spl[b] < spl[b - 1]) atomicExch(&meta->bad, 1);
+}
+
+// ---------------------------------------------------------------- partition
+struct BucketSmem {
+    uint32_t table[1 << TABLE_BITS];
+    uint64_t spl[NSPLIT + 1];
+};
+
+__device__ __forceinline__ void load_bucket_fn(BucketSmem& b, const uint32_t* table, const uint64_t* spl)
+{
+    for (int i = threadIdx.x; i < (1 << TABLE_BITS); i += blockDim.x) b.table[i] = table[i];
+    for (int i = threadIdx.x; i < NSPLIT; i += blockDim.x) b.spl[i] = spl[i];
+}
+
+// The bucket of a key: number of splitters at or below its 53-bit prefix.
+__device__ __forceinline__ int bucket_of(const BucketSmem& b, uint64_t raw, int mode, uint64_t lo53, uint64_t range,
+                                         int sh)
+{
+    const uint64_t e53 = encode_key(raw, mode) >> 11;
+    if (e53 < lo53) return 0;
+    const uint64_t d = e53 - lo53;
+    if (d > range) return count_le(b.spl, e53);
+    const uint32_t tb = b.table[d >> sh];
+    int lo = (int)(tb & 0xffff), hi = (int)(tb >> 16);
+    while (lo < hi) {                              // largest c in [lo, hi] with spl[c-1] <= e53
+        int mid = (lo + hi + 1) >> 1;
+        if (b.spl[mid - 1] <= e53) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Per tile: counts of digit ((bucket >> shift) & 63) -> counts[digit * ntiles + tile].
+// With bucket_counts != nullptr, also the totals of every bucket (per-CTA shared
+// histogram flushed with one atomic per bin).
+__global__ void __launch_bounds__(PART_THREADS)
+    part_hist_kernel(const uint64_t* __restrict__ keys, int64_t n, int mode, const uint32_t* __restrict__ table,
+                     const uint64_t* __restrict__ spl, const LearnMeta* __restrict__ meta, int shift,
+                     uint32_t* __restrict__ counts, int64_t ntiles, unsigned long long* bucket_counts)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    BucketSmem& B = *reinterpret_cast<BucketSmem*>(smem_raw);
+    uint32_t* bcnt = reinterpret_cast<uint32_t*>(smem_raw + sizeof(BucketSmem));
+    __shared__ uint32_t dcnt[64];
+    load_bucket_fn(B, table, spl);
+    if (bucket_counts)
+        for (int i = threadIdx.x; i < NBUCKETS; i += blockDim.x) bcnt[i] = 0;
+    if (threadIdx.x < 64) dcnt[threadIdx.x] = 0;
+    const uint64_t lo53 = meta->lo53, range = meta->range;
+    const int sh = meta->sh;
+    __syncthreads();
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t base = tile * PART_TILE;
+#pragma unroll
+        for (int r = 0; r < PART_ITEMS; ++r) {
+            const int64_t i = base + threadIdx.x + r * PART_THREADS;
+            if (i < n) {
+                const int bk = bucket_of(B, keys[i], mode, lo53, range, sh);
+                atomicAdd(&dcnt[(bk >> shift) & 63], 1u);
+                if (bucket_counts) atomicAdd(&bcnt[bk], 1u);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 64) {
+            counts[(int64_t)threadIdx.x * ntiles + tile] = dcnt[threadIdx.x];
+            dcnt[threadIdx.x] = 0;
+        }
+        __syncthreads();
+    }
+    if (bucket_counts)
+        for (int i = threadIdx.x; i < NBUCKETS; i += blockDim.x)
+            if (bcnt[i]) atomicAdd(&bucket_counts[i], (unsigned long long)bcnt[i]);
+}
+
+// Exclusive scan of row blockIdx.x of counts (ntiles entries) in place; the
+// row total goes to rowtot[row].
+__global__ void __launch_bounds__(1024) row_scan_kernel(uint32_t* counts, int64_t ntiles, unsigned long long* rowtot)
+{
+    __shared__ unsigned long long warp_sum[32];
+    __shared__ unsigned long long s_carry;
+    uint32_t* row = counts + (int64_t)blockIdx.x * ntiles;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    if (t == 0) s_carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < ntiles; base += 1024) {
+        const int64_t i = base + t;
+        const unsigned long long v = i < ntiles ? row[i] : 0;
+        unsigned long long x = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            unsigned long long y = __shfl_up_sync(FULL, x, d);
+            if (lane >= d) x += y;
+        }
+        if (lane == 31) warp_sum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned long long w = warp_sum[lane];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                unsigned long long y = __shfl_up_sync(FULL, w, d);
+                if (lane >= d) w += y;
+            }
+            warp_sum[lane] = w;
+        }
+        __syncthreads();
+        const unsigned long long incl = x + (wid > 0 ? warp_sum[wid - 1] : 0);
+        const unsigned long long carry = s_carry;
+        if (i < ntiles) row[i] = (uint32_t)(carry + incl - v);   // row-local offsets fit: < keys per digit
+        __syncthreads();
+        if (t == 1023) s_carry = carry + incl;
+        __syncthreads();
+    }
+    if (t == 0) rowtot[blockIdx.x] = s_carry;
+}
+
+struct ScatterSmem {
+    BucketSmem bf;
+    uint64_t sk[PART_TILE];
+    uint32_t sv[PART_TILE];
+    uint8_t sd[PART_TILE];
+    uint32_t wcnt[PART_THREADS / 32][64];
+    uint32_t dstart[64];
+    int64_t gbase[64];
+    int64_t dbase[64];
+};
+
+// Stable 64-way scatter of one pass: within a tile every warp ranks its 256
+// consecutive keys in input order (match_any groups, per-warp counters), the
+// tile is laid out by digit in shared memory, and every digit's run is written
+// contiguously to its place: digit base + this tile's offset in the digit.
+__global__ void __launch_bounds__(PART_THREADS)
+    part_scatter_kernel(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sv, uint64_t* __restrict__ dk,
+                        uint32_t* __restrict__ dv, int64_t n, int mode, const uint32_t* __restrict__ table,
+                        const uint64_t* __restrict__ spl, const LearnMeta* __restrict__ meta, int shift,
+                        const uint32_t* __restrict__ counts, int64_t ntiles,
+                        const unsigned long long* __restrict__ rowtot)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    ScatterSmem& S = *reinterpret_cast<ScatterSmem*>(smem_raw);
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    load_bucket_fn(S.bf, table, spl);
+    if (t == 0) {
+        int64_t run = 0;
+        for (int d = 0; d < 64; ++d) {
+            S.dbase[d] = run;
+            run += (int64_t)rowtot[d];
+        }
+    }
+    for (int i = t; i < (PART_THREADS / 32) * 64; i += PART_THREADS) (&S.wcnt[0][0])[i] = 0;
+    const uint64_t lo53 = meta->lo53, range = meta->range;
+    const int sh = meta->sh;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    __syncthreads();
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t base = tile * PART_TILE;
+        uint64_t kk[PART_ITEMS];
+        uint32_t vv[PART_ITEMS];
+        int dd[PART_ITEMS], rr[PART_ITEMS];
+        // this warp's 256 keys, in input order: element base + 256 w + 32 r + lane
+#pragma unroll
+        for (int r = 0; r < PART_ITEMS; ++r) {
+            const int64_t i = base + w * 256 + r * 32 + lane;
+            if (i < n) {
+                kk[r] = sk[i];
+                vv[r] = sv ? sv[i] : 0u;
+                dd[r] = (bucket_of(S.bf, kk[r], mode, lo53, range, sh) >> shift) & 63;
+            } else {
+                dd[r] = 64;                               // past the end: not placed
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < PART_ITEMS; ++r) {
+            const unsigned grp = __match_any_sync(FULL, dd[r]);
+            const int leader = __ffs(grp) - 1;
+            uint32_t pre = 0;
+            if (dd[r] < 64) pre = S.wcnt[w][dd[r]];
+            __syncwarp();
+            if (dd[r] < 64 && lane == leader) S.wcnt[w][dd[r]] = pre + (uint32_t)__popc(grp);
+            __syncwarp();
+            rr[r] = (int)(pre + (uint32_t)__popc(grp & lt_mask));
+        }
+        __syncthreads();
+        if (t < 64) {                                     // tile-local start of each digit
+            uint32_t tot = 0;
+            for (int q = 0; q < PART_THREADS / 32; ++q) tot += S.wcnt[q][t];
+            S.dstart[t] = tot;                            // temporarily the total
+        }
+        __syncthreads();
+        if (t == 0) {
+            uint32_t run = 0;
+            for (int d = 0; d < 64; ++d) {
+                const uint32_t c = S.dstart[d];
+                S.dstart[d] = run;
+                run += c;
+            }
+        }
+        __syncthreads();
+        if (t < 64) {
+            // warp-major prefix inside each digit, then the global base of the digit's run
+            uint32_t run = S.dstart[t];
+            for (int q = 0; q < PART_THREADS / 32; ++q) {
+                const uint32_t c = S.wcnt[q][t];
+                S.wcnt[q][t] = run;
+                run += c;
+            }
+            S.gbase[t] = S.dbase[t] + (int64_t)counts[(int64_t)t * ntiles + tile] - (int64_t)S.dstart[t];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < PART_ITEMS; ++r) {
+            if (dd[r] < 64) {
+                const int pos = (int)S.wcnt[w][dd[r]] + rr[r];
+                S.sk[pos] = kk[r];
+                S.sv[pos] = vv[r];
+                S.sd[pos] = (uint8_t)dd[r];
+            }
+        }
+        __syncthreads();
+        const int cnt = (int)imin64(PART_TILE, n - base);
+        for (int i = t; i < cnt; i += PART_THREADS) {
+            const int64_t g = S.gbase[S.sd[i]] + i;
+            dk[g] = S.sk[i];
+            if (dv) dv[g] = S.sv[i];
+        }
+        __syncthreads();
+        for (int i = t; i < (PART_THREADS / 32) * 64; i += PART_THREADS) (&S.wcnt[0][0])[i] = 0;
+        __syncthreads();
+    }
+}
+
+// Bucket offsets (exclusive scan of the 4096 totals) and bucket statistics.
+__global__ void __launch_bounds__(1024) bucket_offsets_kernel(const unsigned long long* __restrict__ totals,
+                                                              int64_t* __restrict__ off, LearnMeta* meta,
+                                                              float overfull_factor, int64_t n)
+{
+    __shared__ unsigned long long part[1024];
+    __shared__ int64_t smax[1024];
+    __shared__ int snon[1024], sover[1024];
+    constexpr int PER = NBUCKETS / 1024;
+    const int t = threadIdx.x;
+    const double mean = (double)n / NBUCKETS;
+    unsigned long long sum = 0;
+    int64_t mx = 0;
+    int non = 0, over = 0;
+    for (int k = 0; k < PER; ++k) {
+        const unsigned long long c = totals[t * PER + k];
+        sum += c;
+        mx = (int64_t)c > mx ? (int64_t)c : mx;
+        non += c > 0;
+        over += (double)c > overfull_factor * mean;
+    }
+    part[t] = sum;
+    smax[t] = mx;
+    snon[t] = non;
+    sover[t] = over;
+    __syncthreads();
+    if (t == 0) {
+        unsigned long long run = 0;
+        int64_t m = 0;
+        int nn = 0, oo = 0;
+        for (int q = 0; q < 1024; ++q) {
+            const unsigned long long c = part[q];
+            part[q] = run;
+            run += c;
+            m = smax[q] > m ? smax[q] : m;
+            nn += snon[q];
+            oo += sover[q];
+        }
+        off[NBUCKETS] = (int64_t)run;
+        meta->max_bucket = m;
+        meta->nonempty = nn;
+        meta->overfull = oo;
+    }
+    __syncthreads();
+    unsigned long long run = part[t];
+    for (int k = 0; k < PER; ++k) {
+        off[t * PER + k] = (int64_t)run;
+        run += totals[t * PER + k];
+    }
+}
+
+// ---------------------------------------------------------------- host helpers
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+int64_t imin_h(int64_t a, int64_t b) { return a < b ? a : b; }
+
+int sms_now()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 152;
+}
+
+std::once_flag g_learn_attr_once;
+void learn_init_attributes()
+{
+    std::call_once(g_learn_attr_once, [] {
+        cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FitSmem));
+        cudaFuncSetAttribute(part_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(BucketSmem) + NBUCKETS * sizeof(uint32_t)));
+        cudaFuncSetAttribute(part_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(ScatterSmem));
+    });
+}
+
+void init_params_host(float* p)
+{
+    // Layer 1: a bank of steep tanh steps tiling [0, 1]; layer 2: identity plus
+    // a small fixed perturbation; output: equal weights -- a smooth increasing
+    // S-curve from (0, ~0) to (1, ~1) that training reshapes into the CDF.
+    for (int j = 0; j < MH; ++j) {
+        p[P_W1 + j] = 8.0f;
+        p[P_B1 + j] = -8.0f * ((float)j + 0.5f) / (float)MH;
+        p[P_B2 + j] = 0.0f;
+        p[P_W3 + j] = 0.25f;
+        for (int i = 0; i < MH; ++i) {
+            uint32_t h = (uint32_t)(j * MH + i) * 2654435761u;
+            h ^= h >> 15;
+            const float noise = ((float)(h & 0xffff) / 65535.0f - 0.5f) * 0.1f;
+            p[P_W2 + j * MH + i] = (i == j ? 1.0f : 0.0f) + noise;
+        }
+    }
+    p[P_B3] = 0.0f;
+}
+
+// Two allocations: `big` (the partition buffer and the per-tile counts) is
+// released before the bucket sort allocates its own buffer; `small` holds the
+// rest until the end of the call.
+struct LearnLayout {
+    size_t bufk, bufv, counts, big;
+    size_t sample, x, t, params, F, spl, table, meta, rowtot, btot, off, loss, total;
+    int64_t ntiles;
+};
+
+LearnLayout learn_layout(int64_t n, bool with_vals)
+{
+    LearnLayout o{};
+    size_t off = 0;
+    o.ntiles = cdiv(n, PART_TILE);
+    o.bufk = off; off += align256((size_t)n * 8);
+    o.bufv = off; off += with_vals ? align256((size_t)n * 4) : 0;
+    o.counts = off; off += align256((size_t)64 * (size_t)o.ntiles * 4);
+    o.big = off;
+    off = 0;
+    o.sample = off; off += align256((size_t)SAMPLE_M * 8);
+    o.x = off; off += align256((size_t)SAMPLE_M * 4);
+    o.t = off; off += align256((size_t)SAMPLE_M * 4);
+    o.params = off; off += align256((size_t)2 * NP * 4);
+    o.F = off; off += align256((size_t)GRID_G * 4);
+    o.spl = off; off += align256((size_t)(NSPLIT + 1) * 8);
+    o.table = off; off += align256((size_t)(1 << TABLE_BITS) * 4);
+    o.meta = off; off += align256(sizeof(LearnMeta));
+    o.rowtot = off; off += align256(64 * 8);
+    o.btot = off; off += align256((size_t)NBUCKETS * 8);
+    o.off = off; off += align256((size_t)(NBUCKETS + 1) * 8);
+    o.loss = off; off += 256;
+    o.total = off;
+    return o;
+}
+
+}  // namespace
+
+size_t learned_workspace_bytes(int64_t n)
+{
+    const LearnLayout l = learn_layout(n, true);
+    const size_t bucket_sort = segmented_workspace_bytes(n, NBUCKETS);
+    return l.total + (l.big > bucket_sort ? l.big : bucket_sort);   // peak: the two phases do not overlap
+}
+
+// The learned sort on the device (all checks done by the caller).
+int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, const gns_learned_params& prm,
+                        gns_learned_report* rep, cudaStream_t s)
+{
+    learn_init_attributes();
+    const LearnLayout lay = learn_layout(n, vals != nullptr);
+    char* ws = (char*)ws_alloc(lay.total, s);
+    if (!ws) return GNS_ERR_OOM;
+    char* big = (char*)ws_alloc(lay.big, s);
+    if (!big) {
+        ws_free(ws, s);
+        return GNS_ERR_OOM;
+    }
+    int rc = GNS_OK;
+    uint64_t* bufk = (uint64_t*)(big + lay.bufk);
+    uint32_t* bufv = vals ? (uint32_t*)(big + lay.bufv) : nullptr;
+    uint32_t* counts = (uint32_t*)(big + lay.counts);
+    uint64_t* sample = (uint64_t*)(ws + lay.sample);
+    float* x = (float*)(ws + lay.x);
+    float* t = (float*)(ws + lay.t);
+    float* params0 = (float*)(ws + lay.params);
+    float* params1 = params0 + NP;
+    float* F = (float*)(ws + lay.F);
+    uint64_t* spl = (uint64_t*)(ws + lay.spl);
+    uint32_t* table = (uint32_t*)(ws + lay.table);
+    LearnMeta* meta = (LearnMeta*)(ws + lay.meta);
+    unsigned long long* rowtot = (unsigned long long*)(ws + lay.rowtot);
+    unsigned long long* btot = (unsigned long long*)(ws + lay.btot);
+    int64_t* boff = (int64_t*)(ws + lay.off);
+    float* loss = (float*)(ws + lay.loss);
+    const int64_t ntiles = lay.ntiles;
+    const int sms = sms_now();
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (rep)
+        for (auto& e : ev) cudaEventCreate(&e);
+    float hp[NP];
+    init_params_host(hp);
+    const float* trained = params0;
+#define LTRY(x)                     \
+    do {                            \
+        if ((x) != cudaSuccess) {   \
+            rc = GNS_ERR_CUDA;      \
+            goto done;              \
+        }                           \
+    } while (0)
+    if (rep) LTRY(cudaEventRecord(ev[0], s));
+    // 1. sample, sort it, fit the network
+    LTRY(cudaMemcpyAsync(params0, hp, NP * sizeof(float), cudaMemcpyHostToDevice, s));
+    LTRY(cudaMemsetAsync(loss, 0, 256, s));
+    LTRY(launch(K_LEARN_SAMPLE, sample_kernel, dim3(SAMPLE_M / 256), dim3(256), 0, s, (const uint64_t*)keys, n,
+                sample));
+    rc = sort_device(sample, nullptr, SAMPLE_M, mode, 1.0, s);
+    if (rc != GNS_OK) goto done;
+    LTRY(launch(K_LEARN_SAMPLE, fit_inputs_kernel, dim3(SAMPLE_M / 256), dim3(256), 0, s, (const uint64_t*)sample,
+                mode, x, t, meta));
+    if (prm.train_steps > 0) {
+        LTRY(launch(K_LEARN_FIT, mlp_train_kernel, dim3(FIT_CTAS), dim3(FIT_THREADS), sizeof(FitSmem), s,
+                    (const float*)x, (const float*)t, (int64_t)SAMPLE_M, (const float*)params0, params1, loss,
+                    prm.train_steps, prm.batch, prm.learning_rate));
+        trained = params1;
+    }
+    if (rep) LTRY(cudaEventRecord(ev[1], s));
+    // 2. splitters, table, two stable 64-way passes
+    LTRY(launch(K_LEARN_SPLIT, grid_eval_kernel, dim3(256), dim3(256), 0, s,
+                prm.train_steps > 0 ? trained : (const float*)nullptr, F));
+    LTRY(launch(K_LEARN_SPLIT, running_max_kernel, dim3(1), dim3(1024), 0, s, F));
+    LTRY(launch(K_LEARN_SPLIT, splitter_kernel, dim3(cdiv(NSPLIT, 256)), dim3(256), 0, s, (const float*)F, meta, spl));
+    LTRY(launch(K_LEARN_SPLIT, table_kernel, dim3((1 << TABLE_BITS) / 256), dim3(256), 0, s, (const uint64_t*)spl,
+                meta, table));
+    LTRY(cudaMemsetAsync(btot, 0, NBUCKETS * 8, s));
+    for (int pass = 0; pass < 2; ++pass) {
+        const int shift = pass == 0 ? 0 : 6;
+        const uint64_t* src = pass == 0 ? keys : bufk;
+        const uint32_t* srcv = pass == 0 ? vals : bufv;
+        uint64_t* dst = pass == 0 ? bufk : keys;
+        uint32_t* dstv = pass == 0 ? bufv : vals;
+        const int64_t grid = imin_h(ntiles, (int64_t)sms * 2);
+        LTRY(launch(K_LEARN_HIST, part_hist_kernel, dim3((unsigned)grid), dim3(PART_THREADS),
+                    sizeof(BucketSmem) + NBUCKETS * sizeof(uint32_t), s, src, n, mode, (const uint32_t*)table,
+                    (const uint64_t*)spl, (const LearnMeta*)meta, shift, counts, ntiles,
+                    pass == 0 ? btot : (unsigned long long*)nullptr));
+        LTRY(launch(K_LEARN_SCAN, row_scan_kernel, dim3(64), dim3(1024), 0, s, counts, ntiles, rowtot));
+        LTRY(launch(K_LEARN_SCATTER, part_scatter_kernel, dim3((unsigned)grid), dim3(PART_THREADS),
+                    sizeof(ScatterSmem), s, src, srcv, dst, dstv, n, mode, (const uint32_t*)table,
+                    (const uint64_t*)spl, (const LearnMeta*)meta, shift, (const uint32_t*)counts, ntiles,
+                    (const unsigned long long*)rowtot));
+    }
+    LTRY(launch(K_LEARN_VERIFY, bucket_offsets_kernel, dim3(1), dim3(1024), 0, s, (const unsigned long long*)btot,
+                boff, meta, prm.overfull_factor, n));
+    if (rep) LTRY(cudaEventRecord(ev[2], s));
+    ws_free(big, s);
+    big = nullptr;
+    // 3. every bucket is a segment
+    rc = segmented_sort_direct(keys, vals, boff, NBUCKETS, n, mode, s);
+    if (rc != GNS_OK) goto done;
+    if (rep) {
+        LTRY(cudaEventRecord(ev[3], s));
+        LearnMeta hm;
+        float hl = 0.f;
+        LTRY(cudaMemcpyAsync(&hm, meta, sizeof(hm), cudaMemcpyDeviceToHost, s));
+        LTRY(cudaMemcpyAsync(&hl, loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+        LTRY(cudaStreamSynchronize(s));
+        rep->fallback = 0;
+        rep->nonempty_buckets = hm.nonempty;
+        rep->max_bucket = hm.max_bucket;
+        rep->overfull_buckets = hm.overfull;
+        rep->final_loss = hl;
+        cudaEventElapsedTime(&rep->fit_ms, ev[0], ev[1]);
+        cudaEventElapsedTime(&rep->partition_ms, ev[1], ev[2]);
+        cudaEventElapsedTime(&rep->bucket_sort_ms, ev[2], ev[3]);
+        if (hm.bad) rc = GNS_ERR_INTERNAL;
+    }
+#undef LTRY
+done:
+    if (big) ws_free(big, s);
+    ws_free(ws, s);
+    if (rep)
+        for (auto& e : ev) cudaEventDestroy(e);
+    return rc;
+}
+
+}  // namespace gns
+
+using namespace gns;
+
+extern "C" {
+
+void gns_mlp_init_params(float* params_host)
+{
+    if (params_host) init_params_host(params_host);
+}
+
+int gns_mlp_forward(const float* params, const float* x, int64_t m, float* y, gns_stream_t stream)
+{
+    if (!params || m < 0 || (m > 0 && (!x || !y))) return GNS_ERR_INVALID;
+    if (m == 0) return GNS_OK;
+    return launch(K_MLP_FWD, mlp_forward_kernel, dim3(256), dim3(256), 0, (cudaStream_t)stream, params, x, m, y) ==
+                   cudaSuccess
+               ? GNS_OK
+               : GNS_ERR_CUDA;
+}
+
+int gns_mlp_loss_grad(const float* params, const float* x, const float* t, int64_t m, float* grad, float* loss,
+                      gns_stream_t stream)
+{
+    if (!params || m <= 0 || !x || !t || !grad || !loss) return GNS_ERR_INVALID;
+    return launch(K_MLP_BWD, mlp_loss_grad_kernel, dim3(1), dim3(256), 0, (cudaStream_t)stream, params, x, t, m,
+                  grad, loss) == cudaSuccess
+               ? GNS_OK
+               : GNS_ERR_CUDA;
+}
+
+int gns_mlp_train(const float* x, const float* t, int64_t m, const float* params_in, float* params_out,
+                  float* loss_out, int steps, int batch, float learning_rate, gns_stream_t stream)
+{
+    if (!x || !t || !params_in || !params_out || m <= 0 || (m & (m - 1)) || steps < 0) return GNS_ERR_INVALID;
+    if (batch <= 0 || batch % (FIT_CTAS * FIT_THREADS / 32) != 0) return GNS_ERR_INVALID;
+    learn_init_attributes();
+    return launch(K_MLP_ADAM, mlp_train_kernel, dim3(FIT_CTAS), dim3(FIT_THREADS), sizeof(FitSmem),
+                  (cudaStream_t)stream, x, t, m, params_in, params_out, loss_out, steps, batch, learning_rate) ==
+                   cudaSuccess
+               ? GNS_OK
+               : GNS_ERR_CUDA;
+}
+
+int gns_learned_sort(double* keys, uint32_t* payload, int64_t n, int order, double buffer_fraction,
+                     const gns_learned_params* params, gns_learned_report* report, gns_stream_t stream)
+{
+    gns_learned_params prm = {256, 1024, 1e-2f, 4.0f};
+    if (params) prm = *params;
+    if (prm.train_steps < 0 || prm.batch <= 0 || prm.batch % 512 != 0 || !(prm.learning_rate > 0.f) ||
+        !(prm.overfull_factor > 0.f))
+        return GNS_ERR_INVALID;
+    if (n < 0 || (order != GNS_ASCENDING && order != GNS_DESCENDING) || isnan(buffer_fraction) ||
+        buffer_fraction < 0.0)
+        return GNS_ERR_INVALID;
+    if (n > 0 && !keys) return GNS_ERR_INVALID;
+    if (((uintptr_t)keys & 7) || ((uintptr_t)payload & 3)) return GNS_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (report) memset(report, 0, sizeof(*report));
+    if (buffer_fraction < 1.0 || n < (1ll << 20)) {
+        // the partition needs a full buffer and enough keys to pay for the fit
+        if (report) report->fallback = 1;
+        int rc = gns_sort(keys, payload, n, order, buffer_fraction, stream);
+        if (rc == GNS_OK && report) rc = gns_stream_status(stream);
+        return rc;
+    }
+    const int mode = order == GNS_DESCENDING ? MODE_DESC : 0;
+    int rc = learned_sort_device((uint64_t*)keys, payload, n, mode, prm, report, s);
+    return finish_call(rc, s);
+}
+
+}  // extern "C"

@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(THREADS)
 {
     constexpr int T = THREADS * ITEMS;
     if (skip_all(ctl)) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     SmemKV<T>& sm = *reinterpret_cast<SmemKV<T>*>(smem_raw);
     __shared__ int64_t s_base, s_seg_end;
     __shared__ int s_k;
@@ -510,6 +510,21 @@ int segmented_sort_device(uint64_t* keys, uint32_t* vals, const int64_t* off, in
 }
 
 size_t segmented_workspace_bytes(int64_t n, int64_t nseg) { return seg_layout(n, nseg, true).total; }
+
+// Segmented sort without tuning or graph capture (schedule 0), for callers that
+// build the segments themselves on the device (the learned-splitter sort).
+int segmented_sort_direct(uint64_t* keys, uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, int mode,
+                          cudaStream_t s)
+{
+    if (nseg == 0 || n <= 1) return GNS_OK;
+    seg_init_attributes();
+    const SegLayout lay = seg_layout(n, nseg, vals != nullptr);
+    char* ws = (char*)ws_alloc(lay.total, s);
+    if (!ws) return GNS_ERR_OOM;
+    cudaError_t e = seg_enqueue(keys, vals, off, nseg, n, mode, kCandidates[0], ws, lay, s);
+    ws_free(ws, s);
+    return e == cudaSuccess ? GNS_OK : GNS_ERR_CUDA;
+}
 
 int segmented_schedule_of(int64_t n, int64_t nseg, const void* off)
 {

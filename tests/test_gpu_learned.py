@@ -1,0 +1,187 @@
+"""The learned-splitter sort and its network's kernels.
+
+* forward, loss and gradient of the network match the float64 oracle
+  (oracle/mlp.py, itself pinned by finite differences) within float32 error;
+* one Adam step of the on-device trainer matches the oracle's Adam step;
+* training reduces the loss;
+* the learned sort is bit-exact against the oracle's stable sort (it must be,
+  whatever the network learned), including ties, NaNs, signed zeros, both
+  orders, keys only, and its fallbacks;
+* the trained network balances the buckets far better than evenly spaced
+  splitters (what the network gains over the method without it);
+* the full learned workload: 2^28 float64 keys from the three-part mixture.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+from paper_2402_01816_gb300 import inputs
+from tests.gpu_util import assert_bitexact, need_gpu, to_dev_keys, to_dev_payload, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _rand_params(seed):
+    rng = np.random.default_rng(seed)
+    import paper_2402_01816_gb300 as g
+    p = g.gns_mlp_init_params().astype(np.float64)
+    p += rng.normal(0, 0.05, p.size)
+    return p.astype(np.float32)
+
+
+def test_forward_matches_oracle():
+    need_gpu()
+    import paper_2402_01816_gb300 as g
+    p = _rand_params(1)
+    x = np.random.default_rng(2).random(5000).astype(np.float32)
+    y = g.gns_mlp_forward(torch.from_numpy(p).cuda(), torch.from_numpy(x).cuda()).cpu().numpy()
+    want, _ = mlp.forward(p.astype(np.float64), x.astype(np.float64))
+    assert np.max(np.abs(y - want)) < 2e-5
+
+
+def test_loss_and_gradient_match_oracle():
+    need_gpu()
+    import paper_2402_01816_gb300 as g
+    p = _rand_params(3)
+    rng = np.random.default_rng(4)
+    x = rng.random(4096).astype(np.float32)
+    t = np.sort(rng.random(4096)).astype(np.float32)
+    loss, grad = g.gns_mlp_loss_grad(torch.from_numpy(p).cuda(), torch.from_numpy(x).cuda(),
+                                     torch.from_numpy(t).cuda())
+    wl, wg = mlp.loss_grad(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64))
+    assert abs(loss.item() - wl) <= 1e-4 * abs(wl) + 1e-7
+    grad = grad.cpu().numpy()
+    scale = np.max(np.abs(wg))
+    assert np.max(np.abs(grad - wg)) <= 2e-3 * scale
+    # every block of the parameter vector, not just the largest entries
+    for a, b in [(mlp.W1, mlp.B1), (mlp.B1, mlp.W2), (mlp.W2, mlp.B2), (mlp.B2, mlp.W3), (mlp.W3, mlp.B3)]:
+        s = np.max(np.abs(wg[a:b])) + 1e-12
+        assert np.max(np.abs(grad[a:b] - wg[a:b])) <= 5e-3 * s, (a, b)
+
+
+def test_one_adam_step_matches_oracle():
+    need_gpu()
+    import paper_2402_01816_gb300 as g
+    m, batch = 1 << 12, 1024
+    p = _rand_params(5)
+    rng = np.random.default_rng(6)
+    x = np.sort(rng.random(m)).astype(np.float32)
+    t = ((np.arange(m) + 0.5) / m).astype(np.float32)
+    out, loss = g.gns_mlp_train(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda(), torch.from_numpy(p).cuda(),
+                                steps=1, batch=batch, learning_rate=1e-2)
+    idx = (np.arange(batch, dtype=np.uint64) * np.uint64(40503)) & np.uint64(m - 1)
+    wl, wg = mlp.loss_grad(p.astype(np.float64), x[idx].astype(np.float64), t[idx].astype(np.float64))
+    want, _, _ = mlp.adam_step(p.astype(np.float64), wg, np.zeros(p.size), np.zeros(p.size), 1, lr=1e-2)
+    got = out.cpu().numpy()
+    # the first Adam step moves every parameter by about lr * sign(g); entries with
+    # a tiny gradient may flip sign in float32, so compare where |g| is not tiny
+    big = np.abs(wg) > 1e-3 * np.max(np.abs(wg))
+    assert np.max(np.abs(got[big] - want[big])) < 1e-4
+    assert abs(loss.item() - wl) <= 1e-3 * abs(wl) + 1e-7
+
+
+def _key53(keys):
+    """53-bit prefixes of order-mapped float64 keys (input preparation only)."""
+    b = keys.view(np.uint64)
+    enc = np.where(b >> np.uint64(63), ~b, b | np.uint64(1 << 63))
+    return enc >> np.uint64(11)
+
+
+def test_training_reduces_loss():
+    need_gpu()
+    import paper_2402_01816_gb300 as g
+    m = 1 << 16
+    e = _key53(np.sort(inputs.mixture_keys(m, seed=9))).astype(np.float64)
+    x = ((e - e[0]) / (e[-1] - e[0])).astype(np.float32)
+    t = ((np.arange(m) + 0.5) / m).astype(np.float32)
+    p0 = torch.from_numpy(g.gns_mlp_init_params()).cuda()
+    xt, tt = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    l0, _ = g.gns_mlp_loss_grad(p0, xt, tt)
+    p1, _ = g.gns_mlp_train(xt, tt, p0, steps=256)
+    l1, _ = g.gns_mlp_loss_grad(p1, xt, tt)
+    assert l1.item() < 0.2 * l0.item(), (l0.item(), l1.item())
+
+
+def _learned(keys, order=0, with_payload=True, **kw):
+    import paper_2402_01816_gb300 as g
+    n = keys.size
+    pay = inputs.index_payload(n)
+    kt = to_dev_keys(keys)
+    pt = to_dev_payload(pay) if with_payload else None
+    rep = g.gns_learned_sort(kt, pt, order=order, report=True, **kw)
+    assert g.gns_stream_status() == 0
+    want_k, want_p = oracle.stable_sort(keys, pay if with_payload else None, oracle.DESC if order else oracle.ASC)
+    got_p = None if pt is None else pt.cpu().numpy().view(np.uint32)
+    assert_bitexact(kt.cpu().numpy(), got_p, want_k, want_p)
+    return rep
+
+
+N = (1 << 20) + 4099
+
+
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("pattern", ["mixture", "uniform", "ties", "permut", "asc_noise", "desc"])
+def test_learned_exact(pattern, order):
+    need_gpu()
+    rep = _learned(inputs.make_keys(pattern, N, seed=11), order=order)
+    assert rep["fallback"] == 0 and rep["nonempty_buckets"] >= 1
+
+
+def test_learned_edge_keys_and_keys_only():
+    need_gpu()
+    alpha = inputs.edge_alphabet()
+    rng = np.random.default_rng(12)
+    keys = np.concatenate([alpha[rng.integers(0, alpha.size, N // 2)], rng.normal(size=N - N // 2)])
+    _learned(keys, order=0)
+    _learned(keys, order=1, with_payload=False)
+    _learned(np.full(N, 3.0))                                 # all equal: one bucket
+    _learned(np.where(np.arange(N) % 2 == 0, -0.0, 0.0))      # signed zeros are distinct keys
+
+
+def test_learned_fallbacks():
+    need_gpu()
+    rep = _learned(inputs.make_keys("mixture", 5000, seed=1))             # too small
+    assert rep["fallback"] == 1
+    rep = _learned(inputs.make_keys("mixture", N, seed=1), buffer_fraction=0.5)
+    assert rep["fallback"] == 1
+    rep = _learned(inputs.make_keys("mixture", N, seed=1), train_steps=0)  # no network
+    assert rep["fallback"] == 0
+
+
+def test_network_gain_over_even_splitters():
+    """What the trained network gains over splitters spread evenly in the
+    normalised key space (the method without it): on log-normal keys it cuts the
+    largest bucket several-fold; on the three-part mixture (whose point masses,
+    e.g. ~6% of all keys equal to 1.0, no splitter can divide) it puts keys
+    into many more buckets and shortens the bucket sort."""
+    need_gpu()
+    rng = np.random.default_rng(13)
+    logn = np.exp(rng.normal(0.0, 2.0, 1 << 22))
+    trained = _learned(logn)
+    even = _learned(logn, train_steps=0)
+    assert trained["max_bucket"] < 0.5 * even["max_bucket"], (trained, even)
+    mix = inputs.make_keys("mixture", 1 << 22, seed=13)
+    trained = _learned(mix)
+    even = _learned(mix, train_steps=0)
+    assert trained["nonempty_buckets"] > 2 * even["nonempty_buckets"], (trained, even)
+    assert trained["bucket_sort_ms"] < even["bucket_sort_ms"], (trained, even)
+
+
+def test_full_learned_workload():
+    """2^28 float64 keys from the mixture: sorted, stable, a permutation, and
+    sampled output positions from the oracle."""
+    need_gpu()
+    import paper_2402_01816_gb300 as g
+    from tests.test_gpu_fullsize import check_sorted_stable
+    n = 1 << 28
+    keys = inputs.make_keys("mixture", n, seed=0)
+    kt = to_dev_keys(keys)
+    pt = to_dev_payload(inputs.index_payload(n))
+    rep = g.gns_learned_sort(kt, pt, report=True)
+    assert g.gns_stream_status() == 0 and rep["fallback"] == 0
+    k_out = kt.cpu().numpy()
+    p_out = pt.cpu().numpy().view(np.uint32)
+    del kt, pt
+    torch.cuda.empty_cache()
+    check_sorted_stable(keys, k_out, p_out, samples=6)
