@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--n", type=int, default=N_FULL, help="keys per sort (default 2^27)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the learned-vs-plain and batched-vs-plain comparisons")
     return ap.parse_args()
 
 
@@ -68,26 +70,25 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(files):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2402_01816_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, fn), "rb") as f:
-                h.update(fn.encode() + f.read())
+    for fn in files:
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources (else None)."""
+    """DRAM bytes per launch from the committed ncu record, if it was taken on
+    the current sources of that kernel (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
     e = d.get(kernel)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(e.get("files", [])):
         return None
     return e.get("bytes_per_launch")
 
@@ -191,6 +192,100 @@ def run_reference(args, ws, rank):
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ comparisons
+def _time_ms(fn, restore, reps=3):
+    import torch
+    ts = []
+    for _ in range(reps):
+        restore()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def learned_vs_plain(dev, n=1 << 28):
+    """gns_learned_sort against gns_sort (100% tier) on the three-part mixture."""
+    import torch
+    import paper_2402_01816_gb300 as g
+    from paper_2402_01816_gb300 import inputs
+    keys = torch.from_numpy(inputs.make_keys("mixture", n, seed=0)).to(dev)
+    pay = torch.from_numpy(inputs.index_payload(n).view(np.int32)).to(dev)
+    kt, pt = torch.empty_like(keys), torch.empty_like(pay)
+
+    def restore():
+        kt.copy_(keys)
+        pt.copy_(pay)
+    restore()
+    rep = g.gns_learned_sort(kt, pt, report=True)          # warm-up + report
+    restore()
+    g.gns_sort(kt, pt)
+    t_learned = _time_ms(lambda: g.gns_learned_sort(kt, pt), restore)
+    t_even = _time_ms(lambda: g.gns_learned_sort(kt, pt, train_steps=0), restore)
+    t_plain = _time_ms(lambda: g.gns_sort(kt, pt), restore)
+    if g.gns_stream_status() != 0:
+        raise RuntimeError("device status error in learned_vs_plain")
+    del keys, pay, kt, pt
+    torch.cuda.empty_cache()
+    return {"workload": "learned-splitter sort: 2^28 float64 keys (40% log-normal sigma 2, 30% Zipf s=1.2 "
+                        "over 2^16 integers, 30% mix of 8 Gaussians) + uint32 index payload, 4096 buckets",
+            "learned_ms": t_learned, "plain_ms": t_plain, "even_splitters_ms": t_even,
+            "learned_gkeys_s": n / t_learned / 1e6, "plain_gkeys_s": n / t_plain / 1e6,
+            "speedup_vs_plain": t_plain / t_learned, "speedup_vs_even_splitters": t_even / t_learned,
+            "report": rep}
+
+
+def batched_vs_plain(dev, nseg=65536, per_segment_sample=2048):
+    """gns_segmented_sort (one graph launch) against one gns_sort call per segment
+    (timed on the first `per_segment_sample` segments and scaled by key count)
+    and against one gns_sort of the whole array (same volume, not segmented)."""
+    import torch
+    import paper_2402_01816_gb300 as g
+    from paper_2402_01816_gb300 import inputs
+    keys_h, pay_h, off_h = inputs.segments(nseg, seed=0)
+    n = keys_h.size
+    keys = torch.from_numpy(keys_h).to(dev)
+    pay = torch.from_numpy(pay_h.view(np.int32)).to(dev)
+    off = torch.from_numpy(off_h).to(dev)
+    kt, pt = torch.empty_like(keys), torch.empty_like(pay)
+
+    def restore():
+        kt.copy_(keys)
+        pt.copy_(pay)
+    restore()
+    g.gns_segmented_sort(kt, pt, off)                       # tunes + captures the graph
+    launches0 = g.gns_launch_count()
+    t_seg = _time_ms(lambda: g.gns_segmented_sort(kt, pt, off), restore)
+    kernels_per_call = (g.gns_launch_count() - launches0) // 3
+    sched = g.gns_segmented_schedule(n, off)
+    t_whole = _time_ms(lambda: g.gns_sort(kt, pt), restore)
+    m = min(per_segment_sample, nseg)
+    sub_n = int(off_h[m])
+
+    def per_segment():
+        for s_ in range(m):
+            a, b = int(off_h[s_]), int(off_h[s_ + 1])
+            g.gns_sort(kt[a:b], pt[a:b])
+    t_sub = _time_ms(per_segment, restore, reps=2)
+    t_per_seg = t_sub * nseg / m
+    if g.gns_stream_status() != 0:
+        raise RuntimeError("device status error in batched_vs_plain")
+    del keys, pay, off, kt, pt
+    torch.cuda.empty_cache()
+    return {"workload": f"batched segmented sort: {nseg} segments, log-normal lengths (median 2^10, "
+                        f"clipped 16..2^20), {n} int64 keys uniform over the full range + uint32 payload",
+            "segmented_ms": t_seg, "segmented_gkeys_s": n / t_seg / 1e6, "schedule": sched,
+            "kernels_in_graph": kernels_per_call,
+            "per_segment_gns_sort_ms_est": t_per_seg,
+            "per_segment_estimate": f"{m} segments timed ({sub_n} keys), scaled by segment count",
+            "plain_whole_array_ms": t_whole,
+            "speedup_vs_per_segment": t_per_seg / t_seg, "speedup_vs_plain_whole_array": t_whole / t_seg}
 
 
 # ------------------------------------------------------------------ our arm
@@ -364,6 +459,10 @@ def run_ours(args, ws, rank, local):
                "h2d_bytes_per_step": n * 12 * len(combos), "d2h_bytes_per_step": n * 12 * len(combos),
                "entry_point": "gns_sort_host (pinned host buffers, copies inside the timed call)"}
 
+    extras = {}
+    if not args.no_extras and args.n == N_FULL:
+        extras["learned_vs_plain"] = learned_vs_plain(dev)
+        extras["batched_vs_plain"] = batched_vs_plain(dev)
     if rank != 0:
         return
     cpu = None if args.no_cpu_baseline or ws > 1 else cpu_baseline()
@@ -375,7 +474,7 @@ def run_ours(args, ws, rank, local):
                        "n_per_sort": n, "sorts_per_step": len(combos), "parallelism": f"replicas{ws}",
                        "l2": "inputs larger than L2 (1.5 GiB per sort), no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks, "kernels": kernels, "detail": detail}
+            "clocks": clocks, "kernels": kernels, "detail": detail, **extras}
     print(json.dumps(line), flush=True)
 
 
