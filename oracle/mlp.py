@@ -4,10 +4,14 @@ The paper has no learned component; this restates, in float64 NumPy, what the
 library's learned path computes, so that the GPU kernels can be compared with
 it step by step:
 
-* the network: 1 input, two tanh layers of 32 units, one sigmoid output;
+* the network: 1 input, two tanh layers of 32 units, one tanh output unit;
   parameters packed as [w1(32), b1(32), W2(32x32, row j = inputs of unit j),
-  b2(32), w3(32), b3(1)] -- 1153 numbers;
-* the loss: mean squared error to a target CDF value;
+  b2(32), w3(32), b3(1)] -- 1153 numbers.  It is the second stage of the CDF
+  model: its input is the first-stage coordinate x (linear interpolation
+  through 64 sample-quantile intervals) and its output the correction r, so
+  that the CDF estimate is x + r / 64 (the correction stays inside one
+  first-stage interval);
+* the loss: mean squared error to the target correction 64 (t - x);
 * its gradient (backpropagation written out by hand) -- pinned in the tests
   by central finite differences of the loss, which share no code with it;
 * one Adam step;
@@ -31,15 +35,24 @@ def unpack(p):
     return (p[W1:B1], p[B1:W2], p[W2:B2].reshape(H, H), p[B2:W3], p[W3:B3], p[B3])
 
 
+NKNOTS = 64
+
+
 def forward(p, x):
-    """y = sigmoid(w3 . tanh(W2 tanh(w1 x + b1) + b2) + b3) for every x."""
+    """y = tanh(w3 . tanh(W2 tanh(w1 x + b1) + b2) + b3) for every x."""
     w1, b1, w2, b2, w3, b3 = unpack(p)
     x = np.asarray(x, dtype=np.float64)
     h1 = np.tanh(np.outer(x, w1) + b1)            # (m, H)
     h2 = np.tanh(h1 @ w2.T + b2)                  # (m, H)
     z3 = h2 @ w3 + b3                             # (m,)
-    y = 1.0 / (1.0 + np.exp(-z3))
+    y = np.tanh(z3)
     return y, (x, h1, h2)
+
+
+def cdf_estimate(p, x):
+    """The two-stage CDF estimate x + net(x) / 64."""
+    y, _ = forward(p, x)
+    return np.asarray(x, dtype=np.float64) + y / NKNOTS
 
 
 def loss(p, x, t):
@@ -54,7 +67,7 @@ def loss_grad(p, x, t):
     t = np.asarray(t, dtype=np.float64)
     m = x.size
     dy = 2.0 * (y - t) / m                       # dL/dy
-    dz3 = dy * y * (1.0 - y)                     # sigmoid'
+    dz3 = dy * (1.0 - y * y)                     # tanh'
     g_w3 = h2.T @ dz3
     g_b3 = dz3.sum()
     dz2 = np.outer(dz3, w3) * (1.0 - h2 ** 2)    # (m, H)

@@ -20,11 +20,13 @@ def test_forward_closed_forms():
     p[mlp.W3:mlp.B3] = 0.0
     p[mlp.B3] = 0.0
     y, _ = mlp.forward(p, np.linspace(0, 1, 7))
-    assert np.all(y == 0.5)                       # sigmoid(0)
+    assert np.all(y == 0.0)                       # tanh(0): no correction
+    assert np.array_equal(mlp.cdf_estimate(p, [0.25, 0.5]), [0.25, 0.5])
     p = np.zeros(mlp.NPARAM)
-    p[mlp.B3] = np.log(3.0)                       # sigmoid(log 3) = 3/4
+    p[mlp.B3] = np.log(3.0) / 2                   # tanh(log(3)/2) = 1/2
     y, _ = mlp.forward(p, [0.3])
-    assert abs(y[0] - 0.75) < 1e-15
+    assert abs(y[0] - 0.5) < 1e-15
+    assert abs(mlp.cdf_estimate(p, [0.3])[0] - (0.3 + 0.5 / 64)) < 1e-15
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
