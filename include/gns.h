@@ -188,19 +188,29 @@ void gns_segmented_release(gns_stream_t stream);
  *
  * gns_learned_sort sorts float64 keys like gns_sort at the 100% tier, in three
  * phases:
- *   1. fit: 2^16 keys sampled at even strides are sorted; an FP32 MLP
- *      (1 -> 32 tanh -> 32 tanh -> 1 sigmoid) is trained on the device to the
- *      sample's empirical CDF, as a function of the 53-bit prefix of the
- *      order-mapped key normalised to [0, 1] (Adam, mean squared error).
+ *   1. fit: 2^16 keys sampled at even strides are sorted.  The CDF model has
+ *      two stages: a closed-form first stage, linear interpolation through the
+ *      sample quantiles i/64 of the 53-bit prefix of the order-mapped key
+ *      (it removes the empty stretches of the key space), and an FP32 MLP
+ *      (1 -> 32 tanh -> 32 tanh -> 1 tanh) trained on the device (Adam, mean
+ *      squared error) to the residual correction r = 64 (t - x) of that
+ *      coordinate x against the sample's empirical CDF t; the estimate is
+ *      x + r / 64.
  *   2. partition: the network, evaluated on a 2^16-point grid and made monotone
- *      by a running maximum, proposes 4095 splitters (its inverse at j/4096).
+ *      by a running maximum, proposes 4095 splitters (its inverse at j/4096);
+ *      where two splitters coincide (a point mass of the key distribution), the
+ *      next one is lowered to one prefix above them, so the mass gets a bucket
+ *      of its own.
  *      A key's bucket is the number of splitters at or below its 53-bit prefix
  *      -- an integer, monotone function of the key, so equal keys share a
  *      bucket and the concatenation of stably sorted buckets is exactly the
  *      stable sort, however good or bad the network is.  The 4096-way stable
  *      partition is two 64-way stable scatter passes (low, then high 6 bits of
  *      the bucket).
- *   3. bucket sort: every bucket is a segment for the segmented sort; a bucket
+ *   3. bucket sort: every bucket is a segment for the segmented sort, except
+ *      buckets whose keys are all bit-identical, which a stable partition has
+ *      already left in their final order (the DIET idea of the paper's
+ *      "DIET-method" section: an all-tied part needs no sorting); a bucket
  *      that came out larger than `overfull_factor` times the mean is simply
  *      sorted by more merge levels of the same merge path (the plain merge
  *      path is the fallback for it), and if the splitters were not
@@ -211,8 +221,8 @@ void gns_segmented_release(gns_stream_t stream);
  */
 typedef struct {
     int train_steps;         /* Adam steps (default 256); 0 = no network:
-                                splitters evenly spaced in the normalised key
-                                space (the method without the learned part)  */
+                                the first stage alone places the splitters
+                                (the method without the network)             */
     int batch;               /* samples per step, multiple of 512 (default 1024) */
     float learning_rate;     /* default 1e-2                                  */
     float overfull_factor;   /* bucket counted overfull above this x mean (4) */
@@ -223,6 +233,8 @@ typedef struct {
     int nonempty_buckets;
     int64_t max_bucket;      /* largest bucket (keys)                          */
     int overfull_buckets;
+    int tied_buckets;        /* buckets whose keys are all equal: left as
+                                they are (already the stable order)           */
     float final_loss;        /* training loss of the last step                 */
     float fit_ms, partition_ms, bucket_sort_ms;   /* per-phase device time     */
 } gns_learned_report;

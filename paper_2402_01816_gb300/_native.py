@@ -166,7 +166,8 @@ class LearnedParams(ctypes.Structure):
 
 class LearnedReport(ctypes.Structure):
     _fields_ = [("fallback", ctypes.c_int), ("nonempty_buckets", ctypes.c_int), ("max_bucket", ctypes.c_int64),
-                ("overfull_buckets", ctypes.c_int), ("final_loss", ctypes.c_float), ("fit_ms", ctypes.c_float),
+                ("overfull_buckets", ctypes.c_int), ("tied_buckets", ctypes.c_int), ("final_loss", ctypes.c_float),
+                ("fit_ms", ctypes.c_float),
                 ("partition_ms", ctypes.c_float), ("bucket_sort_ms", ctypes.c_float)]
 
 

@@ -94,7 +94,7 @@ int segmented_sort_device(uint64_t* keys, uint32_t* vals, const int64_t* off, in
                           cudaStream_t s);
 size_t segmented_workspace_bytes(int64_t n, int64_t nseg);
 int segmented_sort_direct(uint64_t* keys, uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, int mode,
-                          cudaStream_t s);
+                          const uint8_t* skip, cudaStream_t s);
 size_t learned_workspace_bytes(int64_t n);
 
 }  // namespace gns

@@ -32,7 +32,7 @@ constexpr int SAMPLE_M = 1 << 16;     // sample size (power of two)
 constexpr int GRID_G = 1 << 16;       // grid for inverting the fitted CDF
 constexpr int NBUCKETS = 4096;
 constexpr int NSPLIT = NBUCKETS - 1;
-constexpr int TABLE_BITS = 13;        // bins of the key -> bucket-range table
+constexpr int TABLE_BITS = 22;        // bins of the key -> bucket-range table (global, L2-resident)
 constexpr int PART_TILE = 2048;       // keys per partition tile
 constexpr int PART_THREADS = 256;
 constexpr int PART_ITEMS = PART_TILE / PART_THREADS;
@@ -65,8 +65,9 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-// Forward pass of one sample by one warp, lane j = hidden unit j.  Returns y
-// in every lane; keeps this lane's activations and all of layer 1.
+// Forward pass of one sample by one warp, lane j = hidden unit j.  Returns the
+// network output y = tanh(...) in every lane (the second-stage correction,
+// see first_stage); keeps this lane's activations and all of layer 1.
 __device__ __forceinline__ float net_forward(const NetSmem& s, float x, float& h1j, float& h2j, float (&h1)[MH])
 {
     const int j = threadIdx.x & 31;
@@ -79,7 +80,7 @@ __device__ __forceinline__ float net_forward(const NetSmem& s, float x, float& h
     }
     h2j = tanhf(z);
     const float z3 = warp_sum(s.p[P_W3 + j] * h2j) + s.p[P_B3];
-    return 1.0f / (1.0f + expf(-z3));
+    return tanhf(z3);
 }
 
 // Per-lane gradient accumulators: lane j holds unit j's entries; dw2[i] is
@@ -103,7 +104,7 @@ __device__ __forceinline__ void net_backward(const NetSmem& s, float x, float t,
     const int j = threadIdx.x & 31;
     const float e = y - t;
     g.loss += e * e * scale;
-    const float dz3 = 2.0f * e * scale * y * (1.0f - y);
+    const float dz3 = 2.0f * e * scale * (1.0f - y * y);
     g.w3 = fmaf(dz3, h2j, g.w3);
     g.b3 += dz3;
     const float dz2 = dz3 * s.p[P_W3 + j] * (1.0f - h2j * h2j);
@@ -268,14 +269,51 @@ __global__ void __cluster_dims__(FIT_CTAS, 1, 1) __launch_bounds__(FIT_THREADS)
 }
 
 // ---------------------------------------------------------------- splitters
+constexpr int NKNOTS = 64;            // first stage: 64 intervals between sample quantiles
+
 struct LearnMeta {
     uint64_t lo53;        // 53-bit prefix of the smallest sample key
     uint64_t range;       // prefix of the largest minus lo53 (>= 1)
     int sh;               // table bin = (prefix - lo53) >> sh
     int bad;              // splitters not non-decreasing (never expected)
     int64_t max_bucket;
-    int nonempty, overfull;
+    int nonempty, overfull, tied;
+    uint64_t knot[NKNOTS + 1];   // prefixes of the sample quantiles i/64
 };
+
+// First stage of the CDF model: linear interpolation through the 65 sample
+// quantiles (a closed-form fit that removes the empty stretches of the key
+// space); returns a coordinate in [0, 1] that the network maps to the CDF.
+__device__ __forceinline__ float first_stage(const LearnMeta* m, uint64_t e53)
+{
+    const uint64_t* k = m->knot;
+    if (e53 <= k[0]) return 0.0f;
+    if (e53 >= k[NKNOTS]) return 1.0f;
+    int lo = 0, hi = NKNOTS - 1;                   // largest i < 64 with k[i] <= e53
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (k[mid] <= e53) lo = mid;
+        else hi = mid - 1;
+    }
+    const uint64_t a = k[lo], b = k[lo + 1];
+    const double frac = b > a ? (double)(e53 - a) / (double)(b - a) : 0.0;
+    return (float)(((double)lo + (frac < 1.0 ? frac : 1.0)) / NKNOTS);
+}
+
+// Inverse of the first stage: the prefix at coordinate x (monotone in x).
+__device__ __forceinline__ uint64_t first_stage_inverse(const LearnMeta* m, double x)
+{
+    const uint64_t* k = m->knot;
+    if (x <= 0.0) return k[0];
+    if (x >= 1.0) return k[NKNOTS];
+    int i = (int)(x * NKNOTS);
+    if (i > NKNOTS - 1) i = NKNOTS - 1;
+    const double frac = x * NKNOTS - i;
+    const uint64_t a = k[i], b = k[i + 1];
+    uint64_t off = (uint64_t)ceil(frac * (double)(b - a));
+    if (off > b - a) off = b - a;
+    return a + off;
+}
 
 __global__ void sample_kernel(const uint64_t* __restrict__ keys, int64_t n, uint64_t* __restrict__ sample)
 {
@@ -283,15 +321,18 @@ __global__ void sample_kernel(const uint64_t* __restrict__ keys, int64_t n, uint
     if (i < SAMPLE_M) sample[i] = keys[(i * n) / SAMPLE_M];
 }
 
-// Normalised inputs and targets of the sorted sample; meta range.
-__global__ void fit_inputs_kernel(const uint64_t* __restrict__ sample, int mode, float* __restrict__ x,
-                                  float* __restrict__ t, LearnMeta* meta)
+// Range and first-stage knots of the sorted sample (one small block).
+__global__ void fit_meta_kernel(const uint64_t* __restrict__ sample, int mode, LearnMeta* meta)
 {
-    const uint64_t lo = encode_key(sample[0], mode) >> 11;
-    const uint64_t hi = encode_key(sample[SAMPLE_M - 1], mode) >> 11;
-    const uint64_t range = hi > lo ? hi - lo : 1;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = threadIdx.x;
+    if (i <= NKNOTS) {
+        const int64_t pos = i < NKNOTS ? (int64_t)i * (SAMPLE_M / NKNOTS) : SAMPLE_M - 1;
+        meta->knot[i] = encode_key(sample[pos], mode) >> 11;
+    }
     if (i == 0) {
+        const uint64_t lo = encode_key(sample[0], mode) >> 11;
+        const uint64_t hi = encode_key(sample[SAMPLE_M - 1], mode) >> 11;
+        const uint64_t range = hi > lo ? hi - lo : 1;
         meta->lo53 = lo;
         meta->range = range;
         int sh = 0;
@@ -299,16 +340,25 @@ __global__ void fit_inputs_kernel(const uint64_t* __restrict__ sample, int mode,
         meta->sh = sh;
         meta->bad = 0;
     }
+}
+
+// Training pairs: first-stage coordinate x of every sample key, and the
+// correction the network should output there: 64 (F - x), F = (i + 1/2) / m
+// the sample's empirical CDF.
+__global__ void fit_inputs_kernel(const uint64_t* __restrict__ sample, int mode, float* __restrict__ x,
+                                  float* __restrict__ t, const LearnMeta* meta)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < SAMPLE_M) {
-        const uint64_t e = encode_key(sample[i], mode) >> 11;
-        const double d = (double)(e > lo ? e - lo : 0) / (double)range;
-        x[i] = (float)(d < 1.0 ? d : 1.0);
-        t[i] = ((float)i + 0.5f) / (float)SAMPLE_M;
+        const float xi = first_stage(meta, encode_key(sample[i], mode) >> 11);
+        x[i] = xi;
+        t[i] = (float)NKNOTS * (((float)i + 0.5f) / (float)SAMPLE_M - xi);
     }
 }
 
-// F[g] = net(g / (G - 1)); without a network (params == nullptr) F[g] = g / (G - 1):
-// splitters evenly spaced in the normalised key space.
+// F[g] = x + net(x) / 64 at x = g / (G - 1): the two-stage CDF estimate in the
+// first-stage coordinate; without a network (params == nullptr) F[g] = x, the
+// first stage alone.
 __global__ void __launch_bounds__(256) grid_eval_kernel(const float* __restrict__ params, float* __restrict__ F)
 {
     __shared__ NetSmem s;
@@ -322,8 +372,9 @@ __global__ void __launch_bounds__(256) grid_eval_kernel(const float* __restrict_
     const int gw = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     for (int g = gw; g < GRID_G; g += warps) {
         float h1j, h2j, h1[MH];
-        const float y = net_forward(s, (float)g / (float)(GRID_G - 1), h1j, h2j, h1);
-        if ((threadIdx.x & 31) == 0) F[g] = y;
+        const float xg = (float)g / (float)(GRID_G - 1);
+        const float y = net_forward(s, xg, h1j, h2j, h1);
+        if ((threadIdx.x & 31) == 0) F[g] = xg + y / (float)NKNOTS;
     }
 }
 
@@ -363,10 +414,7 @@ __global__ void splitter_kernel(const float* __restrict__ F, LearnMeta* meta, ui
         if (F[mid] >= q) hi = mid;
         else lo = mid + 1;
     }
-    const uint64_t range = meta->range;
-    uint64_t off = (uint64_t)ceil((double)lo / (double)(GRID_G - 1) * (double)range);
-    if (off > range) off = range;
-    spl[j - 1] = meta->lo53 + off;
+    spl[j - 1] = first_stage_inverse(meta, (double)lo / (double)(GRID_G - 1));
 }
 
 __device__ __forceinline__ int count_le(const uint64_t* spl, uint64_t e53)
@@ -380,97 +428,142 @@ __device__ __forceinline__ int count_le(const uint64_t* spl, uint64_t e53)
     return lo;
 }
 
-// Table bin b -> [bucket of its first prefix, bucket of its last prefix]; also
-// checks that the splitters are non-decreasing.
-__global__ void table_kernel(const uint64_t* __restrict__ spl, LearnMeta* meta, uint32_t* __restrict__ table)
+// Splitter post-processing: a run of equal splitters marks a point mass (many
+// keys with one prefix); the splitter after the run is moved down to the
+// mass's prefix + 1, so that the mass has a bucket of its own (one prefix
+// wide) and can be recognised as all-tied.  Monotonicity is kept.  Also checks
+// that the splitters are non-decreasing.
+__global__ void isolate_masses_kernel(const uint64_t* __restrict__ spl_in, uint64_t* __restrict__ spl, LearnMeta* meta)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= (1 << TABLE_BITS)) return;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= NSPLIT) return;
+    uint64_t v = spl_in[j];
+    if (j >= 2 && spl_in[j - 2] == spl_in[j - 1] && v > spl_in[j - 1] + 1) v = spl_in[j - 1] + 1;
+    spl[j] = v;
+    if (j > 0 && spl_in[j] < spl_in[j - 1]) atomicExch(&meta->bad, 1);
+}
+
+// T[b] = bucket of prefix lo53 + (b << sh), for b = 0 .. 2^22 (the bucket of
+// every key in bin b lies in [T[b], T[b+1]]).  The table is read through L2 by
+// every key; with 2^22 bins over the sample's range it resolves almost every
+// key to one bucket.
+__global__ void __launch_bounds__(256) table_kernel(const uint64_t* __restrict__ spl, const LearnMeta* __restrict__ meta,
+                                                    uint16_t* __restrict__ table)
+{
+    __shared__ uint64_t s_spl[NSPLIT];
+    for (int i = threadIdx.x; i < NSPLIT; i += blockDim.x) s_spl[i] = spl[i];
+    __syncthreads();
     const uint64_t lo53 = meta->lo53, range = meta->range;
     const int sh = meta->sh;
-    const uint64_t dlo = (uint64_t)b << sh;
-    uint32_t entry;
-    if (dlo > range) {
-        entry = (uint32_t)NSPLIT | ((uint32_t)NSPLIT << 16);
-    } else {
-        uint64_t dhi = (((uint64_t)b + 1) << sh) - 1;
-        if (dhi > range) dhi = range;
-        entry = (uint32_t)count_le(spl, lo53 + dlo) | ((uint32_t)count_le(spl, lo53 + dhi) << 16);
+    const int64_t nb = (1ll << TABLE_BITS) + 1;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t d = (uint64_t)b << sh;
+        table[b] = (uint16_t)(d > range ? NSPLIT : count_le(s_spl, lo53 + d));
     }
-    table[b] = entry;
-    if (b > 0 && b < NSPLIT && spl[b] < spl[b - 1]) atomicExch(&meta->bad, 1);
 }
 
 // ---------------------------------------------------------------- partition
-struct BucketSmem {
-    uint32_t table[1 << TABLE_BITS];
-    uint64_t spl[NSPLIT + 1];
-};
-
-__device__ __forceinline__ void load_bucket_fn(BucketSmem& b, const uint32_t* table, const uint64_t* spl)
-{
-    for (int i = threadIdx.x; i < (1 << TABLE_BITS); i += blockDim.x) b.table[i] = table[i];
-    for (int i = threadIdx.x; i < NSPLIT; i += blockDim.x) b.spl[i] = spl[i];
-}
-
-// The bucket of a key: number of splitters at or below its 53-bit prefix.
-__device__ __forceinline__ int bucket_of(const BucketSmem& b, uint64_t raw, int mode, uint64_t lo53, uint64_t range,
-                                         int sh)
+// The bucket of a key: number of splitters at or below its 53-bit prefix, from
+// the table and a short search among the splitters of its bin (shared memory).
+__device__ __forceinline__ int bucket_of(const uint64_t* s_spl, const uint16_t* __restrict__ table, uint64_t raw,
+                                         int mode, uint64_t lo53, uint64_t range, int sh)
 {
     const uint64_t e53 = encode_key(raw, mode) >> 11;
     if (e53 < lo53) return 0;
     const uint64_t d = e53 - lo53;
-    if (d > range) return count_le(b.spl, e53);
-    const uint32_t tb = b.table[d >> sh];
-    int lo = (int)(tb & 0xffff), hi = (int)(tb >> 16);
-    while (lo < hi) {                              // largest c in [lo, hi] with spl[c-1] <= e53
+    if (d > range) return NSPLIT;                     // above every splitter
+    const int64_t b = (int64_t)(d >> sh);
+    int lo = __ldg(&table[b]), hi = __ldg(&table[b + 1]);
+    while (lo < hi) {                                 // largest c in [lo, hi] with spl[c-1] <= e53
         int mid = (lo + hi + 1) >> 1;
-        if (b.spl[mid - 1] <= e53) lo = mid;
+        if (s_spl[mid - 1] <= e53) lo = mid;
         else hi = mid - 1;
     }
     return lo;
 }
 
-// Per tile: counts of digit ((bucket >> shift) & 63) -> counts[digit * ntiles + tile].
-// With bucket_counts != nullptr, also the totals of every bucket (per-CTA shared
-// histogram flushed with one atomic per bin).
-__global__ void __launch_bounds__(PART_THREADS)
-    part_hist_kernel(const uint64_t* __restrict__ keys, int64_t n, int mode, const uint32_t* __restrict__ table,
-                     const uint64_t* __restrict__ spl, const LearnMeta* __restrict__ meta, int shift,
-                     uint32_t* __restrict__ counts, int64_t ntiles, unsigned long long* bucket_counts)
+// Pass-A histogram.  Every key's bucket is evaluated here, once, and written
+// to bid[i]; per tile the counts of its low 6 bits go to
+// counts[digit * ntiles + tile] (per-warp shared sub-histograms), and every
+// bucket's total is accumulated (per-CTA shared histogram, one global atomic
+// per touched bucket at the end).
+constexpr int HIST_THREADS = 256;
+
+__global__ void __launch_bounds__(HIST_THREADS)
+    part_hist_a_kernel(const uint64_t* __restrict__ keys, int64_t n, int mode, const uint16_t* __restrict__ table,
+                       const uint64_t* __restrict__ spl, const LearnMeta* __restrict__ meta,
+                       uint16_t* __restrict__ bid, uint32_t* __restrict__ counts, int64_t ntiles,
+                       unsigned long long* btot)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    BucketSmem& B = *reinterpret_cast<BucketSmem*>(smem_raw);
-    uint32_t* bcnt = reinterpret_cast<uint32_t*>(smem_raw + sizeof(BucketSmem));
-    __shared__ uint32_t dcnt[64];
-    load_bucket_fn(B, table, spl);
-    if (bucket_counts)
-        for (int i = threadIdx.x; i < NBUCKETS; i += blockDim.x) bcnt[i] = 0;
-    if (threadIdx.x < 64) dcnt[threadIdx.x] = 0;
+    __shared__ uint64_t s_spl[NSPLIT];
+    __shared__ uint32_t bcnt[NBUCKETS];
+    __shared__ uint32_t wcnt[HIST_THREADS / 32][64];
+    const int w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < NSPLIT; i += blockDim.x) s_spl[i] = spl[i];
+    for (int i = threadIdx.x; i < NBUCKETS; i += blockDim.x) bcnt[i] = 0;
+    for (int i = threadIdx.x; i < (HIST_THREADS / 32) * 64; i += blockDim.x) (&wcnt[0][0])[i] = 0;
     const uint64_t lo53 = meta->lo53, range = meta->range;
     const int sh = meta->sh;
     __syncthreads();
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t base = tile * PART_TILE;
+        uint64_t raw[PART_TILE / HIST_THREADS];
 #pragma unroll
-        for (int r = 0; r < PART_ITEMS; ++r) {
-            const int64_t i = base + threadIdx.x + r * PART_THREADS;
+        for (int r = 0; r < PART_TILE / HIST_THREADS; ++r) {
+            const int64_t i = base + threadIdx.x + r * HIST_THREADS;
+            raw[r] = i < n ? keys[i] : 0ull;
+        }
+#pragma unroll
+        for (int r = 0; r < PART_TILE / HIST_THREADS; ++r) {
+            const int64_t i = base + threadIdx.x + r * HIST_THREADS;
             if (i < n) {
-                const int bk = bucket_of(B, keys[i], mode, lo53, range, sh);
-                atomicAdd(&dcnt[(bk >> shift) & 63], 1u);
-                if (bucket_counts) atomicAdd(&bcnt[bk], 1u);
+                const int bk = bucket_of(s_spl, table, raw[r], mode, lo53, range, sh);
+                bid[i] = (uint16_t)bk;
+                atomicAdd(&wcnt[w][bk & 63], 1u);
+                atomicAdd(&bcnt[bk], 1u);
             }
         }
         __syncthreads();
         if (threadIdx.x < 64) {
-            counts[(int64_t)threadIdx.x * ntiles + tile] = dcnt[threadIdx.x];
-            dcnt[threadIdx.x] = 0;
+            uint32_t c = 0;
+            for (int q = 0; q < HIST_THREADS / 32; ++q) {
+                c += wcnt[q][threadIdx.x];
+                wcnt[q][threadIdx.x] = 0;
+            }
+            counts[(int64_t)threadIdx.x * ntiles + tile] = c;
         }
         __syncthreads();
     }
-    if (bucket_counts)
-        for (int i = threadIdx.x; i < NBUCKETS; i += blockDim.x)
-            if (bcnt[i]) atomicAdd(&bucket_counts[i], (unsigned long long)bcnt[i]);
+    for (int i = threadIdx.x; i < NBUCKETS; i += blockDim.x)
+        if (bcnt[i]) atomicAdd(&btot[i], (unsigned long long)bcnt[i]);
+}
+
+// Pass-B histogram: per tile, counts of the high 6 bits of the stored bucket ids.
+__global__ void __launch_bounds__(256) part_hist_b_kernel(const uint16_t* __restrict__ bid, int64_t n,
+                                                          uint32_t* __restrict__ counts, int64_t ntiles)
+{
+    __shared__ uint32_t wcnt[8][64];
+    const int w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < 8 * 64; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t base = tile * PART_TILE;
+#pragma unroll
+        for (int r = 0; r < PART_TILE / 256; ++r) {
+            const int64_t i = base + threadIdx.x + r * 256;
+            if (i < n) atomicAdd(&wcnt[w][bid[i] >> 6], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < 64) {
+            uint32_t c = 0;
+            for (int q = 0; q < 8; ++q) {
+                c += wcnt[q][threadIdx.x];
+                wcnt[q][threadIdx.x] = 0;
+            }
+            counts[(int64_t)threadIdx.x * ntiles + tile] = c;
+        }
+        __syncthreads();
+    }
 }
 
 // Exclusive scan of row blockIdx.x of counts (ntiles entries) in place; the
@@ -515,9 +608,9 @@ __global__ void __launch_bounds__(1024) row_scan_kernel(uint32_t* counts, int64_
 }
 
 struct ScatterSmem {
-    BucketSmem bf;
     uint64_t sk[PART_TILE];
     uint32_t sv[PART_TILE];
+    uint16_t sb[PART_TILE];
     uint8_t sd[PART_TILE];
     uint32_t wcnt[PART_THREADS / 32][64];
     uint32_t dstart[64];
@@ -525,21 +618,20 @@ struct ScatterSmem {
     int64_t dbase[64];
 };
 
-// Stable 64-way scatter of one pass: within a tile every warp ranks its 256
-// consecutive keys in input order (match_any groups, per-warp counters), the
-// tile is laid out by digit in shared memory, and every digit's run is written
-// contiguously to its place: digit base + this tile's offset in the digit.
+// Stable 64-way scatter of one pass, digit = (bucket id >> shift) & 63: within a
+// tile every warp ranks its 256 consecutive keys in input order (match_any
+// groups, per-warp counters), the tile is laid out by digit in shared memory,
+// and every digit's run is written contiguously to its place: digit base +
+// this tile's offset in the digit.  The bucket ids travel with the keys when
+// db is given.
 __global__ void __launch_bounds__(PART_THREADS)
-    part_scatter_kernel(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sv, uint64_t* __restrict__ dk,
-                        uint32_t* __restrict__ dv, int64_t n, int mode, const uint32_t* __restrict__ table,
-                        const uint64_t* __restrict__ spl, const LearnMeta* __restrict__ meta, int shift,
-                        const uint32_t* __restrict__ counts, int64_t ntiles,
-                        const unsigned long long* __restrict__ rowtot)
+    part_scatter_kernel(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sv,
+                        const uint16_t* __restrict__ sbid, uint64_t* __restrict__ dk, uint32_t* __restrict__ dv,
+                        uint16_t* __restrict__ dbid, int64_t n, int shift, const uint32_t* __restrict__ counts,
+                        int64_t ntiles, const unsigned long long* __restrict__ rowtot)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    ScatterSmem& S = *reinterpret_cast<ScatterSmem*>(smem_raw);
+    __shared__ ScatterSmem S;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-    load_bucket_fn(S.bf, table, spl);
     if (t == 0) {
         int64_t run = 0;
         for (int d = 0; d < 64; ++d) {
@@ -548,15 +640,13 @@ __global__ void __launch_bounds__(PART_THREADS)
         }
     }
     for (int i = t; i < (PART_THREADS / 32) * 64; i += PART_THREADS) (&S.wcnt[0][0])[i] = 0;
-    const uint64_t lo53 = meta->lo53, range = meta->range;
-    const int sh = meta->sh;
     const unsigned lt_mask = (1u << lane) - 1u;
     __syncthreads();
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t base = tile * PART_TILE;
         uint64_t kk[PART_ITEMS];
         uint32_t vv[PART_ITEMS];
-        int dd[PART_ITEMS], rr[PART_ITEMS];
+        int bb[PART_ITEMS], dd[PART_ITEMS], rr[PART_ITEMS];
         // this warp's 256 keys, in input order: element base + 256 w + 32 r + lane
 #pragma unroll
         for (int r = 0; r < PART_ITEMS; ++r) {
@@ -564,14 +654,23 @@ __global__ void __launch_bounds__(PART_THREADS)
             if (i < n) {
                 kk[r] = sk[i];
                 vv[r] = sv ? sv[i] : 0u;
-                dd[r] = (bucket_of(S.bf, kk[r], mode, lo53, range, sh) >> shift) & 63;
+                bb[r] = sbid[i];
+                dd[r] = (bb[r] >> shift) & 63;
             } else {
+                bb[r] = 0;
                 dd[r] = 64;                               // past the end: not placed
             }
         }
 #pragma unroll
         for (int r = 0; r < PART_ITEMS; ++r) {
-            const unsigned grp = __match_any_sync(FULL, dd[r]);
+            // lanes with the same digit, from one ballot per digit bit (digit 64
+            // marks a lane past the end: bit 6)
+            unsigned grp = FULL;
+#pragma unroll
+            for (int bit = 0; bit < 7; ++bit) {
+                const unsigned bl = __ballot_sync(FULL, (dd[r] >> bit) & 1);
+                grp &= ((dd[r] >> bit) & 1) ? bl : ~bl;
+            }
             const int leader = __ffs(grp) - 1;
             uint32_t pre = 0;
             if (dd[r] < 64) pre = S.wcnt[w][dd[r]];
@@ -581,38 +680,37 @@ __global__ void __launch_bounds__(PART_THREADS)
             rr[r] = (int)(pre + (uint32_t)__popc(grp & lt_mask));
         }
         __syncthreads();
-        if (t < 64) {                                     // tile-local start of each digit
+        if (t < 64) {                                     // each digit: warp-major prefix
             uint32_t tot = 0;
-            for (int q = 0; q < PART_THREADS / 32; ++q) tot += S.wcnt[q][t];
-            S.dstart[t] = tot;                            // temporarily the total
-        }
-        __syncthreads();
-        if (t == 0) {
-            uint32_t run = 0;
-            for (int d = 0; d < 64; ++d) {
-                const uint32_t c = S.dstart[d];
-                S.dstart[d] = run;
-                run += c;
-            }
-        }
-        __syncthreads();
-        if (t < 64) {
-            // warp-major prefix inside each digit, then the global base of the digit's run
-            uint32_t run = S.dstart[t];
             for (int q = 0; q < PART_THREADS / 32; ++q) {
                 const uint32_t c = S.wcnt[q][t];
-                S.wcnt[q][t] = run;
-                run += c;
+                S.wcnt[q][t] = tot;
+                tot += c;
             }
-            S.gbase[t] = S.dbase[t] + (int64_t)counts[(int64_t)t * ntiles + tile] - (int64_t)S.dstart[t];
+            S.dstart[t] = tot;                            // total for now
         }
         __syncthreads();
+        if (t < 32) {                                     // exclusive scan of the 64 totals (one warp)
+            const uint32_t a = S.dstart[2 * t], b = S.dstart[2 * t + 1];
+            uint32_t x = a + b;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, x, d);
+                if (t >= d) x += y;
+            }
+            const uint32_t excl = x - (a + b);
+            S.dstart[2 * t] = excl;
+            S.dstart[2 * t + 1] = excl + a;
+        }
+        __syncthreads();
+        if (t < 64) S.gbase[t] = S.dbase[t] + (int64_t)counts[(int64_t)t * ntiles + tile] - (int64_t)S.dstart[t];
 #pragma unroll
         for (int r = 0; r < PART_ITEMS; ++r) {
             if (dd[r] < 64) {
-                const int pos = (int)S.wcnt[w][dd[r]] + rr[r];
+                const int pos = (int)(S.dstart[dd[r]] + S.wcnt[w][dd[r]]) + rr[r];
                 S.sk[pos] = kk[r];
                 S.sv[pos] = vv[r];
+                S.sb[pos] = (uint16_t)bb[r];
                 S.sd[pos] = (uint8_t)dd[r];
             }
         }
@@ -622,6 +720,7 @@ __global__ void __launch_bounds__(PART_THREADS)
             const int64_t g = S.gbase[S.sd[i]] + i;
             dk[g] = S.sk[i];
             if (dv) dv[g] = S.sv[i];
+            if (dbid) dbid[g] = S.sb[i];
         }
         __syncthreads();
         for (int i = t; i < (PART_THREADS / 32) * 64; i += PART_THREADS) (&S.wcnt[0][0])[i] = 0;
@@ -644,7 +743,8 @@ __global__ void __launch_bounds__(1024) bucket_offsets_kernel(const unsigned lon
     int64_t mx = 0;
     int non = 0, over = 0;
     for (int k = 0; k < PER; ++k) {
-        const unsigned long long c = totals[t * PER + k];
+        const int b = t * PER + k;
+        const unsigned long long c = totals[b];
         sum += c;
         mx = (int64_t)c > mx ? (int64_t)c : mx;
         non += c > 0;
@@ -671,6 +771,7 @@ __global__ void __launch_bounds__(1024) bucket_offsets_kernel(const unsigned lon
         meta->max_bucket = m;
         meta->nonempty = nn;
         meta->overfull = oo;
+        meta->tied = 0;
     }
     __syncthreads();
     unsigned long long run = part[t];
@@ -678,6 +779,66 @@ __global__ void __launch_bounds__(1024) bucket_offsets_kernel(const unsigned lon
         off[t * PER + k] = (int64_t)run;
         run += totals[t * PER + k];
     }
+}
+
+// All-tied buckets (the DIET idea: an all-tied part needs no sorting): only a
+// bucket one prefix wide (splitter b == splitter b-1 + 1) can hold nothing but
+// equal keys.  After the partition the keys are grouped by bucket; each CTA of
+// tied_scan_kernel takes TIED_CHUNK positions, and for every candidate bucket
+// they overlap compares its keys with the bucket's first key, setting diff[b]
+// on a mismatch.  tied_final_kernel then flags the candidates left unmarked.
+constexpr int TIED_CHUNK = 8192;
+
+__device__ __forceinline__ bool tied_candidate(const uint64_t* __restrict__ spl, const int64_t* __restrict__ off, int b)
+{
+    return b >= 1 && b < NSPLIT && spl[b] == spl[b - 1] + 1 && off[b + 1] - off[b] > 1;
+}
+
+__global__ void __launch_bounds__(256) tied_scan_kernel(const uint64_t* __restrict__ keys,
+                                                        const int64_t* __restrict__ off,
+                                                        const uint64_t* __restrict__ spl, int* diff, int64_t n)
+{
+    __shared__ int s_b0, s_b1;
+    const int64_t p0 = (int64_t)blockIdx.x * TIED_CHUNK;
+    const int64_t p1 = p0 + TIED_CHUNK < n ? p0 + TIED_CHUNK : n;
+    if (threadIdx.x == 0) {
+        // bucket holding a position p: the largest b with off[b] <= p
+        int lo = 0, hi = NBUCKETS - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= p0) lo = mid; else hi = mid - 1;
+        }
+        s_b0 = lo;
+        hi = NBUCKETS - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= p1 - 1) lo = mid; else hi = mid - 1;
+        }
+        s_b1 = lo;
+    }
+    __syncthreads();
+    const int b0 = s_b0, b1 = s_b1;
+    for (int b = b0; b <= b1; ++b) {
+        if (!tied_candidate(spl, off, b) || *(volatile int*)&diff[b]) continue;   // uniform over the CTA
+        const int64_t a = off[b] > p0 ? off[b] : p0;
+        const int64_t z = off[b + 1] < p1 ? off[b + 1] : p1;
+        const uint64_t first = keys[off[b]];
+        int d = 0;
+        for (int64_t i = a + threadIdx.x; i < z; i += blockDim.x) d |= keys[i] != first;
+        if (__syncthreads_or(d) && threadIdx.x == 0) diff[b] = 1;
+    }
+}
+
+__global__ void __launch_bounds__(256) tied_final_kernel(const int64_t* __restrict__ off,
+                                                         const uint64_t* __restrict__ spl,
+                                                         const int* __restrict__ diff, uint8_t* __restrict__ tied,
+                                                         LearnMeta* meta)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= NBUCKETS) return;
+    const bool t = tied_candidate(spl, off, b) && !diff[b];
+    tied[b] = t ? 1 : 0;
+    if (t) atomicAdd(&meta->tied, 1);
 }
 
 // ---------------------------------------------------------------- host helpers
@@ -697,23 +858,20 @@ void learn_init_attributes()
 {
     std::call_once(g_learn_attr_once, [] {
         cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FitSmem));
-        cudaFuncSetAttribute(part_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(BucketSmem) + NBUCKETS * sizeof(uint32_t)));
-        cudaFuncSetAttribute(part_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(ScatterSmem));
     });
 }
 
 void init_params_host(float* p)
 {
     // Layer 1: a bank of steep tanh steps tiling [0, 1]; layer 2: identity plus
-    // a small fixed perturbation; output: equal weights -- a smooth increasing
-    // S-curve from (0, ~0) to (1, ~1) that training reshapes into the CDF.
+    // a small fixed perturbation; output layer zero, so the initial correction
+    // is 0 and the initial CDF estimate is the first stage itself.
     for (int j = 0; j < MH; ++j) {
+        const float c = ((float)j + 0.5f) / (float)MH;
         p[P_W1 + j] = 8.0f;
-        p[P_B1 + j] = -8.0f * ((float)j + 0.5f) / (float)MH;
+        p[P_B1 + j] = -8.0f * c;
         p[P_B2 + j] = 0.0f;
-        p[P_W3 + j] = 0.25f;
+        p[P_W3 + j] = 0.0f;
         for (int i = 0; i < MH; ++i) {
             uint32_t h = (uint32_t)(j * MH + i) * 2654435761u;
             h ^= h >> 15;
@@ -728,8 +886,8 @@ void init_params_host(float* p)
 // released before the bucket sort allocates its own buffer; `small` holds the
 // rest until the end of the call.
 struct LearnLayout {
-    size_t bufk, bufv, counts, big;
-    size_t sample, x, t, params, F, spl, table, meta, rowtot, btot, off, loss, total;
+    size_t bufk, bufv, bidA, bidB, counts, big;
+    size_t sample, x, t, params, F, spl, spl_raw, table, meta, rowtot, btot, diff, tied, off, loss, total;
     int64_t ntiles;
 };
 
@@ -740,6 +898,8 @@ LearnLayout learn_layout(int64_t n, bool with_vals)
     o.ntiles = cdiv(n, PART_TILE);
     o.bufk = off; off += align256((size_t)n * 8);
     o.bufv = off; off += with_vals ? align256((size_t)n * 4) : 0;
+    o.bidA = off; off += align256((size_t)n * 2);
+    o.bidB = off; off += align256((size_t)n * 2);
     o.counts = off; off += align256((size_t)64 * (size_t)o.ntiles * 4);
     o.big = off;
     off = 0;
@@ -749,10 +909,13 @@ LearnLayout learn_layout(int64_t n, bool with_vals)
     o.params = off; off += align256((size_t)2 * NP * 4);
     o.F = off; off += align256((size_t)GRID_G * 4);
     o.spl = off; off += align256((size_t)(NSPLIT + 1) * 8);
-    o.table = off; off += align256((size_t)(1 << TABLE_BITS) * 4);
+    o.table = off; off += align256(((size_t)(1 << TABLE_BITS) + 1) * 2);
+    o.spl_raw = off; off += align256((size_t)(NSPLIT + 1) * 8);
     o.meta = off; off += align256(sizeof(LearnMeta));
     o.rowtot = off; off += align256(64 * 8);
     o.btot = off; off += align256((size_t)NBUCKETS * 8);
+    o.diff = off; off += align256((size_t)NBUCKETS * 4);
+    o.tied = off; off += align256((size_t)NBUCKETS);
     o.off = off; off += align256((size_t)(NBUCKETS + 1) * 8);
     o.loss = off; off += 256;
     o.total = off;
@@ -792,10 +955,15 @@ int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, con
     float* params1 = params0 + NP;
     float* F = (float*)(ws + lay.F);
     uint64_t* spl = (uint64_t*)(ws + lay.spl);
-    uint32_t* table = (uint32_t*)(ws + lay.table);
+    uint16_t* table = (uint16_t*)(ws + lay.table);
+    uint64_t* spl_raw = (uint64_t*)(ws + lay.spl_raw);
     LearnMeta* meta = (LearnMeta*)(ws + lay.meta);
     unsigned long long* rowtot = (unsigned long long*)(ws + lay.rowtot);
     unsigned long long* btot = (unsigned long long*)(ws + lay.btot);
+    uint16_t* bidA = (uint16_t*)(big + lay.bidA);
+    uint16_t* bidB = (uint16_t*)(big + lay.bidB);
+    uint8_t* tied = (uint8_t*)(ws + lay.tied);
+    int* diff = (int*)(ws + lay.diff);
     int64_t* boff = (int64_t*)(ws + lay.off);
     float* loss = (float*)(ws + lay.loss);
     const int64_t ntiles = lay.ntiles;
@@ -821,8 +989,9 @@ int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, con
                 sample));
     rc = sort_device(sample, nullptr, SAMPLE_M, mode, 1.0, s);
     if (rc != GNS_OK) goto done;
+    LTRY(launch(K_LEARN_SAMPLE, fit_meta_kernel, dim3(1), dim3(128), 0, s, (const uint64_t*)sample, mode, meta));
     LTRY(launch(K_LEARN_SAMPLE, fit_inputs_kernel, dim3(SAMPLE_M / 256), dim3(256), 0, s, (const uint64_t*)sample,
-                mode, x, t, meta));
+                mode, x, t, (const LearnMeta*)meta));
     if (prm.train_steps > 0) {
         LTRY(launch(K_LEARN_FIT, mlp_train_kernel, dim3(FIT_CTAS), dim3(FIT_THREADS), sizeof(FitSmem), s,
                     (const float*)x, (const float*)t, (int64_t)SAMPLE_M, (const float*)params0, params1, loss,
@@ -834,34 +1003,45 @@ int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, con
     LTRY(launch(K_LEARN_SPLIT, grid_eval_kernel, dim3(256), dim3(256), 0, s,
                 prm.train_steps > 0 ? trained : (const float*)nullptr, F));
     LTRY(launch(K_LEARN_SPLIT, running_max_kernel, dim3(1), dim3(1024), 0, s, F));
-    LTRY(launch(K_LEARN_SPLIT, splitter_kernel, dim3(cdiv(NSPLIT, 256)), dim3(256), 0, s, (const float*)F, meta, spl));
-    LTRY(launch(K_LEARN_SPLIT, table_kernel, dim3((1 << TABLE_BITS) / 256), dim3(256), 0, s, (const uint64_t*)spl,
-                meta, table));
+    LTRY(launch(K_LEARN_SPLIT, splitter_kernel, dim3(cdiv(NSPLIT, 256)), dim3(256), 0, s, (const float*)F, meta,
+                spl_raw));
+    LTRY(launch(K_LEARN_SPLIT, isolate_masses_kernel, dim3(cdiv(NSPLIT, 256)), dim3(256), 0, s,
+                (const uint64_t*)spl_raw, spl, meta));
+    LTRY(launch(K_LEARN_SPLIT, table_kernel, dim3((unsigned)(sms * 4)), dim3(256), 0, s, (const uint64_t*)spl,
+                (const LearnMeta*)meta, table));
     LTRY(cudaMemsetAsync(btot, 0, NBUCKETS * 8, s));
-    for (int pass = 0; pass < 2; ++pass) {
-        const int shift = pass == 0 ? 0 : 6;
-        const uint64_t* src = pass == 0 ? keys : bufk;
-        const uint32_t* srcv = pass == 0 ? vals : bufv;
-        uint64_t* dst = pass == 0 ? bufk : keys;
-        uint32_t* dstv = pass == 0 ? bufv : vals;
-        const int64_t grid = imin_h(ntiles, (int64_t)sms * 2);
-        LTRY(launch(K_LEARN_HIST, part_hist_kernel, dim3((unsigned)grid), dim3(PART_THREADS),
-                    sizeof(BucketSmem) + NBUCKETS * sizeof(uint32_t), s, src, n, mode, (const uint32_t*)table,
-                    (const uint64_t*)spl, (const LearnMeta*)meta, shift, counts, ntiles,
-                    pass == 0 ? btot : (unsigned long long*)nullptr));
+
+    {
+        // pass A: buckets evaluated once (-> bidA), stable scatter by the low 6 bits
+        const int64_t hgrid = imin_h(ntiles, (int64_t)sms * 4);
+        LTRY(launch(K_LEARN_HIST, part_hist_a_kernel, dim3((unsigned)hgrid), dim3(HIST_THREADS), 0, s,
+                    (const uint64_t*)keys, n, mode, (const uint16_t*)table, (const uint64_t*)spl,
+                    (const LearnMeta*)meta, bidA, counts, ntiles, btot));
         LTRY(launch(K_LEARN_SCAN, row_scan_kernel, dim3(64), dim3(1024), 0, s, counts, ntiles, rowtot));
-        LTRY(launch(K_LEARN_SCATTER, part_scatter_kernel, dim3((unsigned)grid), dim3(PART_THREADS),
-                    sizeof(ScatterSmem), s, src, srcv, dst, dstv, n, mode, (const uint32_t*)table,
-                    (const uint64_t*)spl, (const LearnMeta*)meta, shift, (const uint32_t*)counts, ntiles,
-                    (const unsigned long long*)rowtot));
+        const int64_t sgrid = imin_h(ntiles, (int64_t)sms * 3);   // all CTAs resident
+        LTRY(launch(K_LEARN_SCATTER, part_scatter_kernel, dim3((unsigned)sgrid), dim3(PART_THREADS), 0, s,
+                    (const uint64_t*)keys, (const uint32_t*)vals, (const uint16_t*)bidA, bufk, bufv, bidB, n, 0,
+                    (const uint32_t*)counts, ntiles, (const unsigned long long*)rowtot));
+        // pass B: stable scatter by the high 6 bits, back into the caller's arrays
+        LTRY(launch(K_LEARN_HIST, part_hist_b_kernel, dim3((unsigned)imin_h(ntiles, (int64_t)sms * 8)), dim3(256), 0,
+                    s, (const uint16_t*)bidB, n, counts, ntiles));
+        LTRY(launch(K_LEARN_SCAN, row_scan_kernel, dim3(64), dim3(1024), 0, s, counts, ntiles, rowtot));
+        LTRY(launch(K_LEARN_SCATTER, part_scatter_kernel, dim3((unsigned)sgrid), dim3(PART_THREADS), 0, s,
+                    (const uint64_t*)bufk, (const uint32_t*)bufv, (const uint16_t*)bidB, keys, vals,
+                    (uint16_t*)nullptr, n, 6, (const uint32_t*)counts, ntiles, (const unsigned long long*)rowtot));
     }
     LTRY(launch(K_LEARN_VERIFY, bucket_offsets_kernel, dim3(1), dim3(1024), 0, s, (const unsigned long long*)btot,
                 boff, meta, prm.overfull_factor, n));
+    LTRY(cudaMemsetAsync(diff, 0, NBUCKETS * sizeof(int), s));
+    LTRY(launch(K_LEARN_VERIFY, tied_scan_kernel, dim3((unsigned)cdiv(n, TIED_CHUNK)), dim3(256), 0, s,
+                (const uint64_t*)keys, (const int64_t*)boff, (const uint64_t*)spl, diff, n));
+    LTRY(launch(K_LEARN_VERIFY, tied_final_kernel, dim3(NBUCKETS / 256), dim3(256), 0, s, (const int64_t*)boff,
+                (const uint64_t*)spl, (const int*)diff, tied, meta));
     if (rep) LTRY(cudaEventRecord(ev[2], s));
     ws_free(big, s);
     big = nullptr;
     // 3. every bucket is a segment
-    rc = segmented_sort_direct(keys, vals, boff, NBUCKETS, n, mode, s);
+    rc = segmented_sort_direct(keys, vals, boff, NBUCKETS, n, mode, (const uint8_t*)tied, s);
     if (rc != GNS_OK) goto done;
     if (rep) {
         LTRY(cudaEventRecord(ev[3], s));
@@ -874,6 +1054,7 @@ int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, con
         rep->nonempty_buckets = hm.nonempty;
         rep->max_bucket = hm.max_bucket;
         rep->overfull_buckets = hm.overfull;
+        rep->tied_buckets = hm.tied;
         rep->final_loss = hl;
         cudaEventElapsedTime(&rep->fit_ms, ev[0], ev[1]);
         cudaEventElapsedTime(&rep->partition_ms, ev[1], ev[2]);

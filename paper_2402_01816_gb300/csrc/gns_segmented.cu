@@ -45,13 +45,15 @@ struct SegChunk {
 // ---------------------------------------------------------------- plan
 // rows (each nseg + 1 long): row 0 = small-class tiles, row 1 = big-class tiles,
 // row 2 + p = merge chunks of level p.
+// skip (optional): segments flagged non-zero are left as they are (already in
+// order, e.g. all keys equal) and get no work.
 __global__ void seg_count_kernel(const int64_t* __restrict__ off, int64_t nseg, int L, int64_t small_max,
-                                 int64_t* rows, uint8_t* levels, const int* ctl)
+                                 int64_t* rows, uint8_t* levels, const uint8_t* __restrict__ skip, const int* ctl)
 {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nseg || skip_all(ctl)) return;
     const int64_t stride = nseg + 1;
-    const int64_t len = off[s + 1] - off[s];
+    const int64_t len = (skip && skip[s]) ? 0 : off[s + 1] - off[s];
     const int64_t tiles = (len + SEG_T - 1) / SEG_T;
     int k = 0;
     while ((1ll << k) < tiles) ++k;
@@ -294,7 +296,8 @@ void seg_init_attributes()
 
 // Enqueues the whole segmented sort on s (keys/vals in place, ws laid out by lay).
 cudaError_t seg_enqueue(uint64_t* keys, uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, int mode,
-                        const SegSchedule& sch, char* ws, const SegLayout& lay, cudaStream_t s)
+                        const SegSchedule& sch, char* ws, const SegLayout& lay, cudaStream_t s,
+                        const uint8_t* skip = nullptr)
 {
     int* ctl = (int*)(ws + lay.ctl);
     int* call_err = ctl + 2;
@@ -308,7 +311,7 @@ cudaError_t seg_enqueue(uint64_t* keys, uint32_t* vals, const int64_t* off, int6
     cudaError_t e = cudaMemsetAsync(ctl, 0, 256, s);
     if (e != cudaSuccess) return e;
     e = launch(K_SEG_PLAN, seg_count_kernel, dim3((unsigned)ceil_div(nseg, 256)), dim3(256), 0, s, off, nseg, lay.L,
-               sch.small_max, rows, levels, (const int*)ctl);
+               sch.small_max, rows, levels, skip, (const int*)ctl);
     if (e != cudaSuccess) return e;
     e = launch(K_SEG_PLAN, seg_scan_kernel, dim3((unsigned)(2 + lay.L)), dim3(1024), 0, s, rows, nseg,
                (const int*)ctl);
@@ -514,14 +517,14 @@ size_t segmented_workspace_bytes(int64_t n, int64_t nseg) { return seg_layout(n,
 // Segmented sort without tuning or graph capture (schedule 0), for callers that
 // build the segments themselves on the device (the learned-splitter sort).
 int segmented_sort_direct(uint64_t* keys, uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, int mode,
-                          cudaStream_t s)
+                          const uint8_t* skip, cudaStream_t s)
 {
     if (nseg == 0 || n <= 1) return GNS_OK;
     seg_init_attributes();
     const SegLayout lay = seg_layout(n, nseg, vals != nullptr);
     char* ws = (char*)ws_alloc(lay.total, s);
     if (!ws) return GNS_ERR_OOM;
-    cudaError_t e = seg_enqueue(keys, vals, off, nseg, n, mode, kCandidates[0], ws, lay, s);
+    cudaError_t e = seg_enqueue(keys, vals, off, nseg, n, mode, kCandidates[0], ws, lay, s, skip);
     ws_free(ws, s);
     return e == cudaSuccess ? GNS_OK : GNS_ERR_CUDA;
 }
