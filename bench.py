@@ -37,6 +37,8 @@ METRIC = "stable sort Gkeys/s + HBM roofline fraction; learned/batched vs plain 
 UNIT = "Gkeys/s"
 N_FULL = 1 << 27
 TIERS = (1.0, 0.5)
+WORKLOAD = ("plain GPU mergesort, 2^27 float64 keys + uint32 index payload, "
+            "patterns permut/ties/asc_noise/desc, each at 100% and 50% buffer")
 BYTES_PER_ELEM_PASS = 24      # 8 B key + 4 B payload, read and written once per pass
 
 
@@ -49,6 +51,8 @@ def parse_args():
     ap.add_argument("--n", type=int, default=N_FULL, help="keys per sort (default 2^27)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--large", action="store_true",
+                    help="add the 2^31-key 50%%-tier run (about 40 GB on the device, minutes of input generation)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the learned-vs-plain and batched-vs-plain comparisons")
     return ap.parse_args()
@@ -186,9 +190,8 @@ def run_reference(args, ws, rank):
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "plain stable mergesort, float64 keys + uint32 index payload, "
-                                   "patterns permut/ties/asc_noise/desc, 100% and 50% buffer",
-                       "n_per_sort": sample, "full_n": args.n},
+            "config": {"workload": WORKLOAD, "n_per_sort": args.n, "sorts_per_step": 8,
+                       "parallelism": "replicas1", "sample_n_per_sort": sample},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -227,7 +230,7 @@ def learned_vs_plain(dev, n=1 << 28):
     restore()
     g.gns_sort(kt, pt)
     t_learned = _time_ms(lambda: g.gns_learned_sort(kt, pt), restore)
-    t_even = _time_ms(lambda: g.gns_learned_sort(kt, pt, train_steps=0), restore)
+    t_first = _time_ms(lambda: g.gns_learned_sort(kt, pt, train_steps=0), restore)
     t_plain = _time_ms(lambda: g.gns_sort(kt, pt), restore)
     if g.gns_stream_status() != 0:
         raise RuntimeError("device status error in learned_vs_plain")
@@ -235,9 +238,9 @@ def learned_vs_plain(dev, n=1 << 28):
     torch.cuda.empty_cache()
     return {"workload": "learned-splitter sort: 2^28 float64 keys (40% log-normal sigma 2, 30% Zipf s=1.2 "
                         "over 2^16 integers, 30% mix of 8 Gaussians) + uint32 index payload, 4096 buckets",
-            "learned_ms": t_learned, "plain_ms": t_plain, "even_splitters_ms": t_even,
+            "learned_ms": t_learned, "plain_ms": t_plain, "first_stage_only_ms": t_first,
             "learned_gkeys_s": n / t_learned / 1e6, "plain_gkeys_s": n / t_plain / 1e6,
-            "speedup_vs_plain": t_plain / t_learned, "speedup_vs_even_splitters": t_even / t_learned,
+            "speedup_vs_plain": t_plain / t_learned, "speedup_vs_first_stage_only": t_first / t_learned,
             "report": rep}
 
 
@@ -289,7 +292,40 @@ def batched_vs_plain(dev, nseg=65536, per_segment_sample=2048):
 
 
 # ------------------------------------------------------------------ our arm
-def cpu_baseline(n_sample=1 << 22):
+def large_low_memory(dev, n=1 << 31):
+    """2^31 float64 keys + uint32 index payload at the 50% tier (and the 100%
+    tier beside it): time, %RAM and tFootprint per pattern.  The learned path
+    has no 50% form, so its call at buffer_fraction 0.5 is the plain 50% sort."""
+    import torch
+    import paper_2402_01816_gb300 as g
+    from paper_2402_01816_gb300 import inputs
+    out = {"workload": "large low-memory run: 2^31 float64 keys + uint32 index payload (24 GiB), "
+                       "patterns permut and presorted_runs (blocks of 2^16, every 10th sorted)",
+           "learned_at_50pct": "falls back to the plain 50% sort (no learned 50% form)"}
+    pay = torch.arange(n, dtype=torch.int64, device=dev).to(torch.int32)
+    for pattern in ("permut", "presorted_runs"):
+        keys = inputs.make_keys_device(pattern, n, seed=0, device=dev)
+        kt, pt = torch.empty_like(keys), torch.empty_like(pay)
+
+        def restore():
+            kt.copy_(keys)
+            pt.copy_(pay)
+        for bf in (0.5, 1.0):
+            restore()
+            g.gns_sort(kt, pt, buffer_fraction=bf)            # warm-up (workspace pool)
+            t = _time_ms(lambda: g.gns_sort(kt, pt, buffer_fraction=bf), restore, reps=2)
+            ram = 1.0 + g.gns_workspace_bytes(n, bf) / (12.0 * n)
+            out[f"{pattern}@{int(bf * 100)}%"] = {"ms": t, "gkeys_s": n / t / 1e6, "pct_ram": ram,
+                                                 "t_footprint_ms": ram * t}
+        if g.gns_stream_status() != 0:
+            raise RuntimeError("device status error in large_low_memory")
+        del keys, kt, pt
+        torch.cuda.empty_cache()
+        g.gns_release_workspace_cache()
+    return out
+
+
+def cpu_baseline(n_sample=1 << 25):
     import oracle
     from paper_2402_01816_gb300 import inputs
     t, keys = 0.0, 0
@@ -463,14 +499,15 @@ def run_ours(args, ws, rank, local):
     if not args.no_extras and args.n == N_FULL:
         extras["learned_vs_plain"] = learned_vs_plain(dev)
         extras["batched_vs_plain"] = batched_vs_plain(dev)
+    if args.large:
+        extras["large_low_memory"] = large_low_memory(dev)
     if rank != 0:
         return
     cpu = None if args.no_cpu_baseline or ws > 1 else cpu_baseline()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "plain GPU mergesort, 2^27 float64 keys + uint32 index payload, "
-                                   "patterns permut/ties/asc_noise/desc, each at 100% and 50% buffer",
+            "config": {"workload": WORKLOAD,
                        "n_per_sort": n, "sorts_per_step": len(combos), "parallelism": f"replicas{ws}",
                        "l2": "inputs larger than L2 (1.5 GiB per sort), no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

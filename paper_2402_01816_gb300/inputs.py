@@ -114,6 +114,47 @@ def make_keys(pattern: str, n: int, seed: int = 0) -> np.ndarray:
     raise ValueError(f"unknown pattern {pattern!r}")
 
 
+def make_keys_device(pattern: str, n: int, seed: int = 0, device="cuda"):
+    """Device-side generation of the two large-run patterns (permutation-based),
+    for sizes where NumPy's single-threaded shuffle takes minutes: ``permut``
+    (a random permutation of 1..n as float64) and ``presorted_runs`` (the same,
+    with every 10th block of 2**16 ascending), from torch's seeded generator.
+    Same structure as ``make_keys``; not the same numbers."""
+    import torch
+    if n < 2**31:
+        gen = torch.Generator(device=device)
+        gen.manual_seed(int(seed) * 1_000_003 + _PATTERN_IDS[pattern])
+        perm = torch.randperm(n, generator=gen, device=device)
+    elif n & (n - 1) == 0:
+        # torch's shuffle stops at 2**31 - 1 elements: for a power of two, a
+        # seeded composition of bijections of the k-bit integers (multiply by an
+        # odd constant and add, mod 2**k; xor with a right shift) permutes 0..n-1
+        k = n.bit_length() - 1
+        rng = rng_for(pattern, seed)
+        perm = torch.arange(n, dtype=torch.int64, device=device)
+        for _ in range(6):
+            a = 2 * int(rng.integers(1 << 20, 1 << 30)) + 1
+            b = int(rng.integers(0, n))
+            perm.mul_(a).add_(b).bitwise_and_(n - 1)
+            perm.bitwise_xor_(perm >> ((k + 1) // 2))
+    else:
+        raise ValueError("device generator: n >= 2**31 must be a power of two")
+    keys = (perm + 1).to(torch.float64)
+    del perm
+    if pattern == "permut":
+        return keys
+    if pattern == "presorted_runs":
+        blk = 1 << 16
+        nfull = n // blk
+        rows = keys[: nfull * blk].view(nfull, blk)
+        sel = torch.arange(0, nfull, 10, device=device)
+        rows[sel] = torch.sort(rows[sel], dim=1).values
+        if nfull * blk < n and nfull % 10 == 0:
+            keys[nfull * blk:] = torch.sort(keys[nfull * blk:]).values
+        return keys
+    raise ValueError(f"no device generator for {pattern!r}")
+
+
 def mixture_keys(n: int, seed: int = 0) -> np.ndarray:
     rng = rng_for("mixture", seed)
     comp = rng.choice(3, size=n, p=[0.4, 0.3, 0.3])

@@ -64,3 +64,29 @@ def test_small_config_exact():
     want_k, want_p = oracle.stable_sort(keys, pay)
     assert np.array_equal(kt.cpu().numpy().view(np.uint64), want_k.view(np.uint64))
     assert np.array_equal(pt.cpu().numpy().view(np.uint32), want_p)
+
+
+N_LARGE = 1 << 31
+
+
+@pytest.mark.parametrize("pattern", ["permut", "presorted_runs"])
+def test_large_low_memory_run(pattern):
+    """2^31 float64 keys + uint32 index payload at the 50% buffer tier (24 GiB
+    of data, 12 GiB of buffer).  Both patterns are permutations of 1..n, so the
+    sorted keys must be exactly 1..n and the payload must carry every key from
+    its input position; checked on the device."""
+    need_gpu()
+    import paper_2402_01816_gb300 as g
+    kt = inputs.make_keys_device(pattern, N_LARGE, seed=0)
+    pt = torch.arange(N_LARGE, dtype=torch.int64, device="cuda").to(torch.int32)
+    k_in = kt.clone()
+    assert 1.0 + g.gns_workspace_bytes(N_LARGE, 0.5) / (12.0 * N_LARGE) < 1.52     # %RAM
+    g.gns_sort(kt, pt, buffer_fraction=0.5)
+    assert g.gns_stream_status() == 0
+    want = torch.arange(1, N_LARGE + 1, dtype=torch.float64, device="cuda")
+    assert torch.equal(kt, want)
+    del want
+    idx = pt.to(torch.int64) & 0xFFFFFFFF
+    assert torch.equal(k_in[idx], kt)
+    del k_in, kt, pt, idx
+    torch.cuda.empty_cache()
