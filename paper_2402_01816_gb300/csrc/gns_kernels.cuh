@@ -296,6 +296,7 @@ struct Slots {
     uint64_t* k0; uint32_t* v0;   // caller arrays: slots [0, n)
     uint64_t* k1; uint32_t* v1;   // buffer: slots [n, n + b)
     int64_t n;
+    int64_t b;
     __device__ __forceinline__ uint64_t* kp(int64_t s) const { return s < n ? k0 + s : k1 + (s - n); }
     __device__ __forceinline__ uint32_t* vp(int64_t s) const { return s < n ? v0 + s : v1 + (s - n); }
 };

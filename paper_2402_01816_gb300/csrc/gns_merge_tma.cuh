@@ -115,8 +115,8 @@ struct InStage {
 };
 template <int C>
 struct OutBuf {
-    uint64_t k[C];
-    uint32_t v[C];
+    uint64_t k[C + 2];   // room for outputs shifted to the destination's 16-byte phase
+    uint32_t v[C + 4];
 };
 template <int C>
 struct MergeSmem {
@@ -383,33 +383,26 @@ __global__ void __launch_bounds__(THREADS)
 }
 
 // ============================================================ <= 50% tier
-// In-place symmetric merge level with tickets (see frog_merge_kernel for the
-// ordering argument).  A ticket's "inputs loaded" flag is published once its
-// stage's mbarrier has completed; its outputs are stored after every chunk that
-// reads the run elements under them has published.  The prefetched ticket of a
-// CTA is always later than its current one and waits only go to earlier
-// tickets, so no cycle of waits can form.
-template <int C>
-struct FrogChunk {
-    int64_t fi, k, c, w0, w1, oslot;
-    int valid;
-};
+// In-place symmetric merge level.  Chunks are handed out by ticket: within a
+// data-left node from the top chunk down, within a data-right node from the
+// bottom chunk up, so that every chunk that reads a run element lying under
+// chunk c's output holds an earlier ticket than c (the ordering note after
+// frog_partition_kernel).  A ticket's "inputs loaded" flag is published once its
+// stage's mbarrier has completed; its outputs are stored after the flags of
+// every such earlier ticket are set.  A CTA holds at most its current ticket
+// and the next two, always in increasing order, and waits only go to earlier
+// tickets, so no cycle of waits can form.  The flags of all levels share one
+// array: level flags hold the level's epoch (1, 2, ... in launch order) once
+// loaded, so a flag left by an earlier level never reads as loaded.
 
-template <int C>
-__device__ __forceinline__ FrogChunk<C> frog_chunk(int64_t tk, const FrogNode* level, int64_t nch)
-{
-    FrogChunk<C> g;
-    g.k = tk / nch;
-    const int64_t local = tk % nch;
-    const FrogNode x = level[g.k];
-    g.c = x.side == 0 ? nch - 1 - local : local;
-    g.fi = g.k * nch + g.c;
-    g.w0 = g.c * C;
-    g.valid = g.w0 < x.n;
-    g.w1 = g.valid ? imin64(g.w0 + C, x.n) : g.w0;
-    g.oslot = frog_data_slot(x) + g.w0;
-    return g;
-}
+// Everything a ticket's merge needs, precomputed by frog_items_kernel so that
+// the merge loop issues its copies after one independent load.
+struct FrogItem {
+    int64_t ra, rb;        // slot of the first element of the left / right slice
+    int64_t oslot;         // slot of the first output
+    int32_t na, nb;        // slice lengths (0, 0: nothing to do)
+    int32_t dep_lo, dep_hi;   // tickets whose loads must precede the store (dep_hi < dep_lo: none)
+};
 
 // Range [lo, hi] of the chunks of node k that read the run elements chunk c
 // overwrites (hi < lo: none).  A data-left node overwrites left-run indices
@@ -470,30 +463,63 @@ __device__ __forceinline__ int2 frog_dep_range(int64_t c, const FrogNode& x, con
     return r;
 }
 
-// deps[k * nch + c] = frog_dep_range for every chunk of a level (after the
-// partition, before the merge).
-static __global__ void frog_deps_kernel(const FrogNode* __restrict__ level, const FrogNode* __restrict__ child,
-                                 int64_t nnodes, int64_t nch, const int64_t* __restrict__ splits, int2* deps,
-                                 const int* presorted)
+// items[tk] for every ticket tk of a level (after the partition, before the
+// merge): ticket tk = k * nch + local is chunk c = nch - 1 - local of a
+// data-left node k and chunk c = local of a data-right one.
+static __global__ void frog_items_kernel(const FrogNode* __restrict__ level, const FrogNode* __restrict__ child,
+                                         int64_t nnodes, int64_t nch, const int64_t* __restrict__ splits,
+                                         FrogItem* __restrict__ items, int* call_err, const int* presorted)
 {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nnodes * nch || skip_all(presorted)) return;
-    const int64_t k = idx / nch, c = idx % nch;
-    deps[idx] = frog_dep_range(c, level[k], child[2 * k], child[2 * k + 1], splits + k * nch, CHUNK);
+    const int64_t tk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tk >= nnodes * nch || skip_all(presorted)) return;
+    const int64_t k = tk / nch, local = tk % nch;
+    const FrogNode x = level[k];
+    const int64_t c = x.side == 0 ? nch - 1 - local : local;
+    FrogItem it;
+    it.ra = it.rb = it.oslot = 0;
+    it.na = it.nb = 0;
+    it.dep_lo = 0;
+    it.dep_hi = -1;
+    const int64_t w0 = c * CHUNK;
+    if (w0 < x.n) {
+        const int64_t w1 = imin64(w0 + CHUNK, x.n);
+        const FrogNode L = child[2 * k], R = child[2 * k + 1];
+        const int64_t* sp = splits + k * nch;
+        const int64_t a0 = sp[c];
+        const int64_t a1 = (w1 == x.n) ? L.n : sp[c + 1];
+        const int64_t na = a1 - a0, nb = (w1 - a1) - (w0 - a0);
+        if (na < 0 || nb < 0 || na + nb > CHUNK || a0 < 0 || a1 > L.n) {   // splits inconsistent
+            atomicCAS(call_err, 0, GNS_ERR_INTERNAL);
+        } else {
+            it.na = (int32_t)na;
+            it.nb = (int32_t)nb;
+            it.ra = frog_data_slot(L) + a0;
+            it.rb = frog_data_slot(R) + (w0 - a0);
+            it.oslot = frog_data_slot(x) + w0;
+            const int2 r = frog_dep_range(c, x, L, R, sp, CHUNK);
+            if (r.x <= r.y) {
+                const int64_t base = k * nch;
+                it.dep_lo = (int32_t)(x.side == 0 ? base + nch - 1 - r.y : base + r.x);
+                it.dep_hi = (int32_t)(x.side == 0 ? base + nch - 1 - r.x : base + r.y);
+            }
+        }
+    }
+    items[tk] = it;
 }
 
-// Spin until *flag == 1; `poll()` runs in the loop (it publishes the CTA's
+// Spin until *flag == want; `poll()` runs in the loop (it publishes the CTA's
 // prefetched ticket as soon as that ticket's inputs have landed, so that no
 // chain of waits runs through tickets that are loaded but not yet announced).
 template <typename Poll>
-__device__ __forceinline__ bool wait_flag_polling(const int* flag, int* call_err, uint64_t limit_ns, Poll poll)
+__device__ __forceinline__ bool wait_flag_polling(const int* flag, int want, int* call_err, uint64_t limit_ns,
+                                                  Poll poll)
 {
-    if (ld_acquire(flag) == 1) return true;
+    if (ld_acquire(flag) == want) return true;
     const uint64_t t0 = global_ns();
     unsigned sleep_ns = 32;
     for (;;) {
         poll();
-        if (ld_acquire(flag) == 1) return true;
+        if (ld_acquire(flag) == want) return true;
         if (ld_relaxed(call_err) != 0) return false;
         if (global_ns() - t0 > limit_ns) {
             atomicCAS(call_err, 0, GNS_ERR_TIMEOUT);
@@ -506,11 +532,9 @@ __device__ __forceinline__ bool wait_flag_polling(const int* flag, int* call_err
 
 template <int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS)
-    frog_merge_tma_kernel(Slots sl, const FrogNode* __restrict__ level, const FrogNode* __restrict__ child,
-                          int64_t nnodes, int64_t nch, const int64_t* __restrict__ splits,
-                          const int2* __restrict__ deps, int mode, int decode_out,
-                          int* ticket, int* loaded, int* call_err, uint64_t limit_ns, int64_t skip_ticket,
-                          const int* presorted)
+    frog_merge_tma_kernel(Slots sl, const FrogItem* __restrict__ items, int64_t total, int mode, int decode_out,
+                          int* ticket, int* loaded, int epoch, int* call_err, uint64_t limit_ns,
+                          int64_t skip_ticket, const int* presorted)
 {
     constexpr int C = THREADS * ITEMS;
     if (skip_all(presorted)) return;
@@ -518,41 +542,31 @@ __global__ void __launch_bounds__(THREADS)
     MergeSmem<C>& sm = *reinterpret_cast<MergeSmem<C>*>(smem_raw);
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ StagedChunk staged[2];
-    __shared__ int64_t s_tk;
+    __shared__ int64_t s_tk[2];
+    __shared__ int64_t s_after;
     __shared__ int s_ok;
     const int t = threadIdx.x;
     const bool has_vals = sl.v0 != nullptr;
-    const int64_t total = nnodes * nch;
     if (t == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         fence_mbar_init();
-        s_tk = atomicAdd(ticket, 1);
+        s_tk[0] = atomicAdd(ticket, 1);
+        s_tk[1] = s_tk[0] < total ? atomicAdd(ticket, 1) : total;
         s_ok = 1;
     }
     __syncthreads();
-    int64_t tk = s_tk;
+    int64_t tk = s_tk[0], tk_next = s_tk[1];
     if (tk >= total) return;
 
     bool pending[2] = {false, false};
-    auto stage = [&](int slot, const FrogChunk<C>& fc) {
-        int na = 0, nb = 0;
-        int64_t ra = 0, rb = 0;
-        if (fc.valid) {
-            const FrogNode L = child[2 * fc.k], R = child[2 * fc.k + 1];
-            const FrogNode x = level[fc.k];
-            const int64_t a0 = splits[fc.fi];
-            const int64_t a1 = (fc.w1 == x.n) ? L.n : splits[fc.fi + 1];
-            na = (int)(a1 - a0);
-            nb = (int)((fc.w1 - a1) - (fc.w0 - a0));
-            ra = frog_data_slot(L) + a0;
-            rb = frog_data_slot(R) + (fc.w0 - a0);
-            if (na < 0 || nb < 0 || na + nb > C || a0 < 0 || a1 > L.n) {   // splits inconsistent
-                if (t == 0) atomicCAS(call_err, 0, GNS_ERR_INTERNAL);
-                na = nb = 0;
-                ra = rb = 0;
-            }
+    auto stage = [&](int slot, const FrogItem& m) {
+        int na = m.na, nb = m.nb;
+        if (na < 0 || nb < 0 || na + nb > C) {   // inconsistent item: stage nothing
+            if (t == 0) atomicCAS(call_err, 0, GNS_ERR_INTERNAL);
+            na = nb = 0;
         }
+        const int64_t ra = na > 0 ? m.ra : 0, rb = nb > 0 ? m.rb : 0;
         // slices that straddle the caller-array / buffer boundary use plain loads
         const bool pa = na > 0 && ra < sl.n && ra + na > sl.n;
         const bool pb = nb > 0 && rb < sl.n && rb + nb > sl.n;
@@ -563,66 +577,58 @@ __global__ void __launch_bounds__(THREADS)
         pending[slot] = true;
     };
 
-    FrogChunk<C> cur = frog_chunk<C>(tk, level, nch);
+    FrogItem cur = items[tk];
     stage(0, cur);
     bool published_cur = false;   // thread 0's view: cur's flag already set while waiting
     unsigned parity[2] = {0u, 0u};
-    int it = 0;
-    for (;; ++it) {
-        const int cs = it & 1;
-        __syncthreads();                                // s_tk consumed; previous stores read `out`
-        if (t == 0) s_tk = atomicAdd(ticket, 1);
-        __syncthreads();
-        const int64_t tk_next = s_tk;
-        FrogChunk<C> nxt;
-        nxt.valid = 0;
-        if (tk_next < total) {
-            nxt = frog_chunk<C>(tk_next, level, nch);
-            stage(cs ^ 1, nxt);
+    for (int it = 0;; ++it) {
+        const int cs = it & 1, ns = cs ^ 1;
+        const bool has_next = tk_next < total;
+        FrogItem nxt = cur;
+        if (has_next) {
+            nxt = items[tk_next];
+            stage(ns, nxt);
         }
+        bool published_next = false;
         if (t == 0) {
+            s_after = has_next ? atomicAdd(ticket, 1) : total;   // the ticket after next
             if (!mbar_wait(&bars[cs], parity[cs], limit_ns)) {
                 atomicCAS(call_err, 0, GNS_ERR_TIMEOUT);
                 s_ok = 0;
             } else if (tk != skip_ticket && !published_cur) {
-                st_release(&loaded[cur.fi], 1);         // this chunk's inputs are in shared memory
+                st_release(&loaded[tk], epoch);         // this chunk's inputs are in shared memory
             }
             if (ld_relaxed(call_err) != 0) s_ok = 0;
-            bulk_wait_read_all();
+            bulk_wait_read_all();                       // the previous chunk's store has read `out`
+            if (s_ok && cur.dep_lo <= cur.dep_hi) {
+                const unsigned pn = parity[ns];
+                auto poll = [&]() {
+                    if (!published_next && has_next && tk_next != skip_ticket && mbar_try_wait(&bars[ns], pn)) {
+                        st_release(&loaded[tk_next], epoch);
+                        published_next = true;
+                    }
+                };
+                bool ok = true;
+                for (int32_t q = cur.dep_lo; ok && q <= cur.dep_hi; ++q)
+                    ok = wait_flag_polling(&loaded[q], epoch, call_err, limit_ns, poll);
+                if (!ok) s_ok = 0;
+            }
+            fence_proxy_async_global();                 // the bulk store below follows the acquires above
         }
-        bool published_next = false;
         parity[cs] ^= 1u;
         pending[cs] = false;
         __syncthreads();
         if (!s_ok) break;
+        const int64_t tk_after = s_after;
         const StagedChunk g = staged[cs];
         const int cnt = g.na + g.nb;
-        if (cur.valid) {
-            // thread 0 first waits for this chunk's dependencies (overlapping the
-            // other warps' merging), then merges its own outputs
-            if (t == 0) {
-                const int ns = cs ^ 1;
-                auto poll = [&]() {
-                    if (!published_next && tk_next < total && tk_next != skip_ticket &&
-                        mbar_try_wait(&bars[ns], parity[ns])) {
-                        st_release(&loaded[nxt.fi], 1);
-                        published_next = true;
-                    }
-                };
-                const int2 dr = deps[cur.fi];
-                bool ok = true;
-                for (int q = dr.x; ok && q <= dr.y; ++q)
-                    ok = wait_flag_polling(&loaded[cur.k * nch + q], call_err, limit_ns, poll);
-                if (!ok) s_ok = 0;
-                fence_proxy_async_global();             // the bulk store below follows the acquires above
-            }
-            uint64_t k[ITEMS];
-            uint32_t v[ITEMS];
-            const int m = merge_staged<C, ITEMS>(sm.in[cs], g, k, v, has_vals);
-            if (m > 0) write_out<C, ITEMS>(sm.out, k, v, m, has_vals, mode, decode_out);
-            fence_proxy_async_shared();
-            __syncthreads();
-            if (!s_ok) break;
+        uint64_t k[ITEMS];
+        uint32_t v[ITEMS];
+        const int m = merge_staged<C, ITEMS>(sm.in[cs], g, k, v, has_vals);
+        if (m > 0) write_out<C, ITEMS>(sm.out, k, v, m, has_vals, mode, decode_out);
+        fence_proxy_async_shared();
+        __syncthreads();
+        if (cnt > 0) {
             const int64_t o = cur.oslot;
             const bool contiguous = (o + cnt <= sl.n) || (o >= sl.n);
             uint64_t* Dk = sl.kp(o);
@@ -640,8 +646,9 @@ __global__ void __launch_bounds__(THREADS)
                 }
             }
         }
-        if (tk_next >= total) break;
+        if (!has_next) break;
         tk = tk_next;
+        tk_next = tk_after;
         cur = nxt;
         published_cur = published_next;
     }

@@ -11,12 +11,14 @@
 // Keys are encoded (order map) when first read and decoded by the last write.
 #include <stdio.h>
 #include <stdlib.h>
+#include <string.h>
 
 #include <mutex>
 
 #include "gns_internal.h"
 #include "gns_kernels.cuh"
 #include "gns_merge_tma.cuh"
+#include "gns_merge_ws.cuh"
 
 namespace gns {
 
@@ -24,6 +26,10 @@ namespace {
 
 constexpr size_t kSmemTile = sizeof(SmemKV<TILE>);
 constexpr size_t kSmemTma = sizeof(MergeSmem<TMA_CHUNK>);
+template <int S>
+constexpr size_t ws_smem() { return sizeof(WsSmem<WS_CHUNK, S>); }
+template <int S>
+constexpr size_t ws_smem_out() { return sizeof(WsSmemOut<WS_CHUNK, S>); }
 
 int num_sms()
 {
@@ -63,7 +69,7 @@ int64_t frog_chunks(int64_t n, int d) { return ceil_div(ceil_div(n, 1ll << d), C
 
 struct Layout {
     // control words (ints): [0..1] presorted flags, [2] call error
-    size_t ctl, bufk, bufv, splits, deps, nodes, flags, tickets, total;
+    size_t ctl, bufk, bufv, splits, items, nodes, flags, tickets, total;
     size_t flags_bytes, tickets_bytes;
     int L, D;
 };
@@ -87,14 +93,14 @@ Layout make_layout(int64_t n, double bf, bool with_vals)
         o.bufk = off; off += align256((size_t)b * 8);
         o.bufv = off; off += with_vals ? align256((size_t)b * 4) : 0;
         o.nodes = off; off += align256((size_t)((2ll << D) - 1) * sizeof(FrogNode));
-        int64_t max_split = 0, nflags = 1ll << D;   // setup flags: one per leaf
+        int64_t max_split = 0;
         for (int d = 0; d < D; ++d) {
             int64_t e = (1ll << d) * frog_chunks(n, d);
             if (e > max_split) max_split = e;
-            nflags += e;
         }
+        const int64_t nflags = (1ll << D) + max_split;   // one per leaf (setup), one per ticket (all levels)
         o.splits = off; off += align256((size_t)max_split * 8);
-        o.deps = off; off += align256((size_t)max_split * 8);
+        o.items = off; off += align256((size_t)max_split * sizeof(FrogItem));
         o.flags = off; o.flags_bytes = align256((size_t)nflags * 4); off += o.flags_bytes;
         o.tickets = off; o.tickets_bytes = align256((size_t)(D + 1) * 4); off += o.tickets_bytes;
     }
@@ -117,7 +123,104 @@ void init_attributes()
         set_smem(merge_pass_tma_kernel<TMA_THREADS, TMA_ITEMS>, kSmemTma);
         set_smem(frog_setup_kernel<SORT_THREADS, SORT_ITEMS>, kSmemTile);
         set_smem(frog_merge_tma_kernel<TMA_THREADS, TMA_ITEMS>, kSmemTma);
+        set_smem(merge_pass_ws_kernel<2>, ws_smem_out<2>());
+        set_smem(merge_pass_ws_kernel<3>, ws_smem_out<3>());
+        set_smem(merge_pass_ws_kernel<4>, ws_smem_out<4>());
+        set_smem(frog_merge_ws_kernel<2>, ws_smem<2>());
+        set_smem(frog_merge_ws_kernel<3>, ws_smem<3>());
+        set_smem(frog_merge_ws_kernel<4>, ws_smem<4>());
     });
+}
+
+// Merge-level pipeline (GNS_MERGE_PIPE overrides the default):
+//   "tma"  every thread stages and merges (gns_merge_tma.cuh);
+//   "ws2", "ws3", "ws4"  warp-specialised with 2 / 3 / 4 stages
+//   (gns_merge_ws.cuh; default ws2: six CTAs per SM, measured fastest).
+enum MergePipe { PIPE_TMA = 0, PIPE_WS2, PIPE_WS3, PIPE_WS4 };
+
+int merge_pipe()
+{
+    static const int v = [] {
+        const char* e = getenv("GNS_MERGE_PIPE");
+        if (!e) return (int)PIPE_WS2;
+        if (!strcmp(e, "tma")) return (int)PIPE_TMA;
+        if (!strcmp(e, "ws3")) return (int)PIPE_WS3;
+        if (!strcmp(e, "ws4")) return (int)PIPE_WS4;
+        return (int)PIPE_WS2;
+    }();
+    return v;
+}
+
+// Resident CTAs of a kernel at its launch shape, over all SMs.
+template <typename K>
+int64_t resident_ctas(K kernel, int threads, size_t smem)
+{
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, threads, smem) != cudaSuccess || v <= 0) {
+        cudaGetLastError();
+        v = 1;
+    }
+    return (int64_t)v * num_sms();
+}
+
+template <int S>
+cudaError_t launch_plain_level_ws(const uint64_t* sk, const uint32_t* sv, uint64_t* dk, uint32_t* dv, int64_t n,
+                                  int64_t w, int64_t nblocks, const int64_t* splits, int mode, int decode,
+                                  int* call_err, uint64_t limit, const int* skip, cudaStream_t s)
+{
+    static const int64_t cap = resident_ctas(merge_pass_ws_kernel<S>, WS_CONSUMERS + 32, ws_smem_out<S>());
+    const int64_t grid = imin(nblocks, cap);
+    return launch(K_MERGE_PASS, merge_pass_ws_kernel<S>, dim3((unsigned)grid), dim3(WS_CONSUMERS + 32),
+                  ws_smem_out<S>(), s, sk, sv, dk, dv, n, w, nblocks, splits, mode, decode, call_err, limit, skip);
+}
+
+template <int S>
+cudaError_t launch_frog_level_ws(const Slots& sl, const FrogItem* items, int64_t total, int mode, int decode,
+                                 int* ticket, int* loaded, int epoch, int* call_err, uint64_t limit,
+                                 int64_t skip_ticket, const int* skip, cudaStream_t s)
+{
+    static const int64_t cap = resident_ctas(frog_merge_ws_kernel<S>, WS_CONSUMERS + 32, ws_smem<S>());
+    const int64_t grid = imin(total, cap);
+    return launch(K_FROG_MERGE, frog_merge_ws_kernel<S>, dim3((unsigned)grid), dim3(WS_CONSUMERS + 32), ws_smem<S>(),
+                  s, sl, items, total, mode, decode, ticket, loaded, epoch, call_err, limit, skip_ticket, skip);
+}
+
+cudaError_t launch_plain_level(const uint64_t* sk, const uint32_t* sv, uint64_t* dk, uint32_t* dv, int64_t n,
+                               int64_t w, int64_t nblocks, const int64_t* splits, int mode, int decode,
+                               int* call_err, uint64_t limit, const int* skip, cudaStream_t s)
+{
+#define GNS_PLAIN_ARGS sk, sv, dk, dv, n, w, nblocks, splits, mode, decode, call_err, limit, skip, s
+    switch (merge_pipe()) {
+    case PIPE_WS2: return launch_plain_level_ws<2>(GNS_PLAIN_ARGS);
+    case PIPE_WS3: return launch_plain_level_ws<3>(GNS_PLAIN_ARGS);
+    case PIPE_WS4: return launch_plain_level_ws<4>(GNS_PLAIN_ARGS);
+    default: {
+        const int64_t grid = imin(nblocks, (int64_t)num_sms() * TMA_CTAS_PER_SM);
+        return launch(K_MERGE_PASS, merge_pass_tma_kernel<TMA_THREADS, TMA_ITEMS>, dim3((unsigned)grid),
+                      dim3(TMA_THREADS), kSmemTma, s, sk, sv, dk, dv, n, w, nblocks, splits, mode, decode, call_err,
+                      limit, skip);
+    }
+    }
+#undef GNS_PLAIN_ARGS
+}
+
+cudaError_t launch_frog_level(const Slots& sl, const FrogItem* items, int64_t total, int mode, int decode,
+                              int* ticket, int* loaded, int epoch, int* call_err, uint64_t limit, int64_t skip_ticket,
+                              const int* skip, cudaStream_t s)
+{
+#define GNS_FROG_ARGS sl, items, total, mode, decode, ticket, loaded, epoch, call_err, limit, skip_ticket, skip, s
+    switch (merge_pipe()) {
+    case PIPE_WS2: return launch_frog_level_ws<2>(GNS_FROG_ARGS);
+    case PIPE_WS3: return launch_frog_level_ws<3>(GNS_FROG_ARGS);
+    case PIPE_WS4: return launch_frog_level_ws<4>(GNS_FROG_ARGS);
+    default: {
+        const int64_t grid = imin(total, (int64_t)num_sms() * TMA_CTAS_PER_SM);
+        return launch(K_FROG_MERGE, frog_merge_tma_kernel<TMA_THREADS, TMA_ITEMS>, dim3((unsigned)grid),
+                      dim3(TMA_THREADS), kSmemTma, s, sl, items, total, mode, decode, ticket, loaded, epoch,
+                      call_err, limit, skip_ticket, skip);
+    }
+    }
+#undef GNS_FROG_ARGS
 }
 
 #define GNS_TRY(x)                              \
@@ -185,23 +288,21 @@ int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, 
             const int64_t w = (int64_t)TILE << lvl;
             GNS_TRY(launch(K_MERGE_PARTITION, merge_partition_kernel, dim3((unsigned)ceil_div(nblocks, 256)),
                            dim3(256), 0, s, (const uint64_t*)cur_k, n, w, nblocks, splits, skip));
-            const int64_t grid = imin(nblocks, (int64_t)num_sms() * TMA_CTAS_PER_SM);
-            GNS_TRY(launch(K_MERGE_PASS, merge_pass_tma_kernel<TMA_THREADS, TMA_ITEMS>, dim3((unsigned)grid),
-                           dim3(TMA_THREADS), kSmemTma, s, (const uint64_t*)cur_k, (const uint32_t*)cur_v, oth_k,
-                           oth_v, n, w, nblocks, (const int64_t*)splits, mode, (int)(lvl == L - 1), call_err,
-                           wait_limit_ns(), skip));
+            GNS_TRY(launch_plain_level((const uint64_t*)cur_k, (const uint32_t*)cur_v, oth_k, oth_v, n, w, nblocks,
+                                       (const int64_t*)splits, mode, (int)(lvl == L - 1), call_err, wait_limit_ns(),
+                                       skip, s));
             uint64_t* tk = cur_k; cur_k = oth_k; oth_k = tk;
             uint32_t* tv = cur_v; cur_v = oth_v; oth_v = tv;
         }
     } else {
         const int D = lay.D;
         Slots sl;
-        sl.k0 = keys; sl.v0 = vals; sl.n = n;
+        sl.k0 = keys; sl.v0 = vals; sl.n = n; sl.b = n / 2;
         sl.k1 = (uint64_t*)(ws + lay.bufk);
         sl.v1 = vals ? (uint32_t*)(ws + lay.bufv) : nullptr;
         FrogNode* nodes = (FrogNode*)(ws + lay.nodes);
         int64_t* splits = (int64_t*)(ws + lay.splits);
-        int2* deps = (int2*)(ws + lay.deps);
+        FrogItem* items = (FrogItem*)(ws + lay.items);
         int* flags = (int*)(ws + lay.flags);
         int* tickets = (int*)(ws + lay.tickets);
         const uint64_t limit = wait_limit_ns();
@@ -223,16 +324,12 @@ int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, 
             const FrogNode* child = nodes + (2 * nnodes - 1);
             GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel, dim3((unsigned)ceil_div(nnodes * nch, 256)),
                            dim3(256), 0, s, sl, level, child, nnodes, nch, splits, skip));
-            GNS_TRY(launch(K_FROG_PARTITION, frog_deps_kernel, dim3((unsigned)ceil_div(nnodes * nch, 256)),
-                           dim3(256), 0, s, level, child, nnodes, nch, (const int64_t*)splits, deps, skip));
-            const int64_t grid = imin(nnodes * nch, (int64_t)num_sms() * TMA_CTAS_PER_SM);
-            GNS_TRY(launch(K_FROG_MERGE, frog_merge_tma_kernel<TMA_THREADS, TMA_ITEMS>, dim3((unsigned)grid),
-                           dim3(TMA_THREADS), kSmemTma, s, sl, level, child,
-                           nnodes, nch, (const int64_t*)splits, (const int2*)deps, mode, (int)(d == 0), tickets + d,
-                           lflags, call_err,
-                           limit, skip_ticket, skip));
+            GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel, dim3((unsigned)ceil_div(nnodes * nch, 256)),
+                           dim3(256), 0, s, level, child, nnodes, nch, (const int64_t*)splits, items, call_err,
+                           skip));
+            GNS_TRY(launch_frog_level(sl, (const FrogItem*)items, nnodes * nch, mode, (int)(d == 0), tickets + d,
+                                      lflags, D - d, call_err, limit, skip_ticket, skip, s));
             skip_ticket = -1;
-            lflags += nnodes * nch;
         }
     }
     GNS_TRY(publish_call_error(call_err, s));
