@@ -21,6 +21,7 @@
 #include "gns_internal.h"
 #include "gns_kernels.cuh"
 #include "gns_merge_tma.cuh"
+#include "gns_merge_ws.cuh"
 
 namespace gns {
 
@@ -65,8 +66,8 @@ void init_attributes()
     std::call_once(g_attr_once, [] {
         cudaFuncSetAttribute(tile_sort_kernel<SORT_THREADS, SORT_ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(SmemKV<TILE>));
-        cudaFuncSetAttribute(merge_pass_tma_kernel<TMA_THREADS, TMA_ITEMS>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MergeSmem<TMA_CHUNK>));
+        cudaFuncSetAttribute(merge_pass_ws_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(WsSmemOut<WS_CHUNK, 2>));
     });
 }
 
@@ -130,11 +131,11 @@ extern "C" int gns_sort_noalloc(double* keys, uint32_t* payload, int64_t n, int 
         e = launch(K_NOALLOC_SORT, merge_partition_kernel, dim3((unsigned)ceil_div(nblocks, 256)), dim3(256), 0, s,
                    (const uint64_t*)cur_k, n, w, nblocks, splits, (const int*)presorted);
         if (e != cudaSuccess) break;
-        const int64_t grid = nblocks < (int64_t)sms() * TMA_CTAS_PER_SM ? nblocks : (int64_t)sms() * TMA_CTAS_PER_SM;
-        e = launch(K_NOALLOC_SORT, merge_pass_tma_kernel<TMA_THREADS, TMA_ITEMS>, dim3((unsigned)grid),
-                   dim3(TMA_THREADS), sizeof(MergeSmem<TMA_CHUNK>), s, (const uint64_t*)cur_k, (const uint32_t*)cur_v,
-                   oth_k, oth_v, n, w, nblocks, (const int64_t*)splits, mode, (int)(lvl == levels - 1), call_err,
-                   wait_limit_ns(), (const int*)presorted);
+        const int64_t grid = nblocks < (int64_t)sms() * 6 ? nblocks : (int64_t)sms() * 6;
+        e = launch(K_NOALLOC_SORT, merge_pass_ws_kernel<2>, dim3((unsigned)grid), dim3(WS_CONSUMERS + 32),
+                   sizeof(WsSmemOut<WS_CHUNK, 2>), s, (const uint64_t*)cur_k, (const uint32_t*)cur_v, oth_k, oth_v, n,
+                   w, nblocks, (const int64_t*)splits, mode, (int)(lvl == levels - 1), call_err, wait_limit_ns(),
+                   (const int*)presorted);
         uint64_t* tk = cur_k; cur_k = oth_k; oth_k = tk;
         uint32_t* tv = cur_v; cur_v = oth_v; oth_v = tv;
     }

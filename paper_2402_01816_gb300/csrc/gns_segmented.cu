@@ -28,6 +28,7 @@
 #include "gns_internal.h"
 #include "gns_kernels.cuh"
 #include "gns_merge_tma.cuh"
+#include "gns_merge_ws.cuh"
 
 namespace gns {
 
@@ -207,28 +208,52 @@ __global__ void seg_partition_kernel(const uint64_t* __restrict__ keys, const ui
     list[i] = r;
 }
 
-template <int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS)
-    seg_merge_tma_kernel(uint64_t* keys, uint32_t* vals, uint64_t* bufk, uint32_t* bufv,
-                         const SegChunk* __restrict__ list, const int64_t* __restrict__ count, int mode,
-                         int* call_err, uint64_t limit_ns, const int* ctl)
-{
-    if (skip_all(ctl)) return;
-    auto get = [&](int64_t i) {
+// One merge level of the segmented sort, chunk list from seg_partition_kernel,
+// through the warp-specialised pipeline of the plain levels: item i of the
+// list goes to CTA i mod gridDim.x.
+struct SegLevelSrc {
+    uint64_t* keys; uint32_t* vals; uint64_t* bufk; uint32_t* bufv;
+    int64_t n;
+    const SegChunk* list;
+    int64_t count, i;
+    __device__ __forceinline__ bool next(WsLoad& L)
+    {
+        if (i >= count) return false;
         const SegChunk r = list[i];
+        i += gridDim.x;
         const bool fb = r.flags & 1;
         const uint64_t* sk = fb ? bufk : keys;
         const uint32_t* sv = fb ? bufv : vals;
         uint64_t* dk = fb ? keys : bufk;
         uint32_t* dv = fb ? vals : bufv;
-        MergeItem m;
-        m.ak = sk + r.a_src; m.av = sv ? sv + r.a_src : nullptr; m.na = r.na;
-        m.bk = sk + r.b_src; m.bv = sv ? sv + r.b_src : nullptr; m.nb = r.nb;
-        m.dk = dk + r.out0; m.dv = dv ? dv + r.out0 : nullptr;
-        m.decode = (r.flags >> 1) & 1;
-        return m;
-    };
-    merge_items_tma<THREADS, ITEMS>(*count, get, mode, call_err, limit_ns);
+        L.ak = sk + r.a_src; L.av = sv ? sv + r.a_src : nullptr; L.na = r.na;
+        L.bk = sk + r.b_src; L.bv = sv ? sv + r.b_src : nullptr; L.nb = r.nb;
+        L.ak_end = L.bk_end = sk + n;
+        L.av_end = L.bv_end = sv ? sv + n : nullptr;
+        L.plain_a = L.plain_b = false;
+        L.slot_a = L.slot_b = 0;
+        L.dk = dk + r.out0; L.dv = dv ? dv + r.out0 : nullptr;
+        L.oslot = 0;
+        L.decode = (r.flags >> 1) & 1;
+        L.tk = 0;
+        L.dep_lo = 0;
+        L.dep_hi = -1;
+        return true;
+    }
+};
+
+constexpr int SEG_WS_STAGES = 2;
+
+__global__ void __launch_bounds__(WS_CONSUMERS + 32, 6)
+    seg_merge_ws_kernel(uint64_t* keys, uint32_t* vals, uint64_t* bufk, uint32_t* bufv, int64_t n,
+                        const SegChunk* __restrict__ list, const int64_t* __restrict__ count, int mode, int* call_err,
+                        uint64_t limit_ns, const int* ctl)
+{
+    if (skip_all(ctl)) return;
+    const int64_t cnt = *count;
+    if ((int64_t)blockIdx.x >= cnt) return;
+    SegLevelSrc src{keys, vals, bufk, bufv, n, list, cnt, (int64_t)blockIdx.x};
+    ws_merge_out<WS_CONSUMERS, WS_ITEMS, SEG_WS_STAGES>(src, vals != nullptr, mode, call_err, limit_ns);
 }
 
 // ---------------------------------------------------------------- host side
@@ -289,8 +314,8 @@ void seg_init_attributes()
                              (int)sizeof(SmemKV<2048>));
         cudaFuncSetAttribute(seg_tile_kernel<64, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(SmemKV<1024>));
-        cudaFuncSetAttribute(seg_merge_tma_kernel<TMA_THREADS, TMA_ITEMS>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MergeSmem<TMA_CHUNK>));
+        cudaFuncSetAttribute(seg_merge_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(WsSmemOut<WS_CHUNK, SEG_WS_STAGES>));
     });
 }
 
@@ -337,10 +362,9 @@ cudaError_t seg_enqueue(uint64_t* keys, uint32_t* vals, const int64_t* off, int6
                    (const uint64_t*)keys, (const uint64_t*)bufk, off, nseg, prefix, (const uint8_t*)levels, p, list,
                    (const int*)ctl);
         if (e != cudaSuccess) return e;
-        const int64_t grid = lay.max_items < (int64_t)sms * TMA_CTAS_PER_SM ? lay.max_items
-                                                                             : (int64_t)sms * TMA_CTAS_PER_SM;
-        e = launch(K_SEG_MERGE, seg_merge_tma_kernel<TMA_THREADS, TMA_ITEMS>, dim3((unsigned)grid), dim3(TMA_THREADS),
-                   sizeof(MergeSmem<TMA_CHUNK>), s, keys, vals, bufk, bufv, (const SegChunk*)list,
+        const int64_t grid = lay.max_items < (int64_t)sms * 6 ? lay.max_items : (int64_t)sms * 6;
+        e = launch(K_SEG_MERGE, seg_merge_ws_kernel, dim3((unsigned)grid), dim3(WS_CONSUMERS + 32),
+                   sizeof(WsSmemOut<WS_CHUNK, SEG_WS_STAGES>), s, keys, vals, bufk, bufv, n, (const SegChunk*)list,
                    (const int64_t*)(prefix + nseg), mode, call_err, wait_limit_ns(), (const int*)ctl);
         if (e != cudaSuccess) return e;
     }
