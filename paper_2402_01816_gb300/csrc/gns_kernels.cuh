@@ -28,7 +28,15 @@ namespace gns {
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_ITEMS = 16;
 constexpr int TILE = SORT_THREADS * SORT_ITEMS;       // 4096 elements
-constexpr int CHUNK = 1024;                           // outputs per merge chunk
+// Merge levels work in chunks of CHUNK outputs, MERGE_ITEMS per consumer
+// thread (gns_merge_ws.cuh); GNS_MERGE_CONSUMERS may be set at build time.
+#ifndef GNS_MERGE_CONSUMERS
+#define GNS_MERGE_CONSUMERS 256
+#endif
+constexpr int MERGE_CONSUMERS = GNS_MERGE_CONSUMERS;
+constexpr int MERGE_ITEMS = 8;
+constexpr int CHUNK = MERGE_CONSUMERS * MERGE_ITEMS;  // outputs per merge chunk
+static_assert(CHUNK == 1024 || CHUNK == 2048, "merge chunk size");
 constexpr int DETECT_TILE = 4096;
 
 // Shared-memory index with one pad slot per 16 elements: thread t's blocked

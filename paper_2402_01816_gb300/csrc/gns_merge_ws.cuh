@@ -33,10 +33,16 @@
 
 namespace gns {
 
-constexpr int WS_CONSUMERS = 128;
-constexpr int WS_ITEMS = 8;
-constexpr int WS_CHUNK = WS_CONSUMERS * WS_ITEMS;   // 1024 outputs per item
+constexpr int WS_CONSUMERS = MERGE_CONSUMERS;
+constexpr int WS_ITEMS = MERGE_ITEMS;
+constexpr int WS_CHUNK = WS_CONSUMERS * WS_ITEMS;   // outputs per item
 static_assert(WS_CHUNK == CHUNK, "merge chunk size");
+
+// Resident CTAs per SM the S-stage layouts are sized for (shared memory and
+// registers): six 160-thread CTAs with 1024-output stages, three 288-thread
+// CTAs with 2048-output stages.
+template <int S>
+constexpr int ws_ctas_per_sm() { return WS_CONSUMERS == 128 ? (S <= 3 ? 6 : 4) : (S == 2 ? 3 : 2); }
 
 template <int C, int S>
 struct WsSmem {
@@ -669,7 +675,7 @@ struct FrogLevelSrc {
 };
 
 template <int S>
-__global__ void __launch_bounds__(WS_CONSUMERS + 32, S <= 3 ? 6 : 4)
+__global__ void __launch_bounds__(WS_CONSUMERS + 32, ws_ctas_per_sm<S>())
     merge_pass_ws_kernel(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sv, uint64_t* __restrict__ dk,
                          uint32_t* __restrict__ dv, int64_t n, int64_t w, int64_t nblocks,
                          const int64_t* __restrict__ splits, int mode, int decode_out, int* call_err,
@@ -681,7 +687,7 @@ __global__ void __launch_bounds__(WS_CONSUMERS + 32, S <= 3 ? 6 : 4)
 }
 
 template <int S>
-__global__ void __launch_bounds__(WS_CONSUMERS + 32, S <= 3 ? 6 : 4)
+__global__ void __launch_bounds__(WS_CONSUMERS + 32, ws_ctas_per_sm<S>())
     frog_merge_ws_kernel(Slots sl, const FrogItem* __restrict__ items, int64_t total, int mode, int decode_out,
                          int* ticket, int* loaded, int epoch, int* call_err, uint64_t limit_ns, int64_t skip_ticket,
                          const int* presorted)

@@ -131,7 +131,8 @@ extern "C" int gns_sort_noalloc(double* keys, uint32_t* payload, int64_t n, int 
         e = launch(K_NOALLOC_SORT, merge_partition_kernel, dim3((unsigned)ceil_div(nblocks, 256)), dim3(256), 0, s,
                    (const uint64_t*)cur_k, n, w, nblocks, splits, (const int*)presorted);
         if (e != cudaSuccess) break;
-        const int64_t grid = nblocks < (int64_t)sms() * 6 ? nblocks : (int64_t)sms() * 6;
+        const int64_t cap = (int64_t)sms() * ws_ctas_per_sm<2>();
+        const int64_t grid = nblocks < cap ? nblocks : cap;
         e = launch(K_NOALLOC_SORT, merge_pass_ws_kernel<2>, dim3((unsigned)grid), dim3(WS_CONSUMERS + 32),
                    sizeof(WsSmemOut<WS_CHUNK, 2>), s, (const uint64_t*)cur_k, (const uint32_t*)cur_v, oth_k, oth_v, n,
                    w, nblocks, (const int64_t*)splits, mode, (int)(lvl == levels - 1), call_err, wait_limit_ns(),

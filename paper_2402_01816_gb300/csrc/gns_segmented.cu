@@ -244,7 +244,7 @@ struct SegLevelSrc {
 
 constexpr int SEG_WS_STAGES = 2;
 
-__global__ void __launch_bounds__(WS_CONSUMERS + 32, 6)
+__global__ void __launch_bounds__(WS_CONSUMERS + 32, ws_ctas_per_sm<SEG_WS_STAGES>())
     seg_merge_ws_kernel(uint64_t* keys, uint32_t* vals, uint64_t* bufk, uint32_t* bufv, int64_t n,
                         const SegChunk* __restrict__ list, const int64_t* __restrict__ count, int mode, int* call_err,
                         uint64_t limit_ns, const int* ctl)
@@ -362,7 +362,8 @@ cudaError_t seg_enqueue(uint64_t* keys, uint32_t* vals, const int64_t* off, int6
                    (const uint64_t*)keys, (const uint64_t*)bufk, off, nseg, prefix, (const uint8_t*)levels, p, list,
                    (const int*)ctl);
         if (e != cudaSuccess) return e;
-        const int64_t grid = lay.max_items < (int64_t)sms * 6 ? lay.max_items : (int64_t)sms * 6;
+        const int64_t cap = (int64_t)sms * ws_ctas_per_sm<SEG_WS_STAGES>();
+        const int64_t grid = lay.max_items < cap ? lay.max_items : cap;
         e = launch(K_SEG_MERGE, seg_merge_ws_kernel, dim3((unsigned)grid), dim3(WS_CONSUMERS + 32),
                    sizeof(WsSmemOut<WS_CHUNK, SEG_WS_STAGES>), s, keys, vals, bufk, bufv, n, (const SegChunk*)list,
                    (const int64_t*)(prefix + nseg), mode, call_err, wait_limit_ns(), (const int*)ctl);

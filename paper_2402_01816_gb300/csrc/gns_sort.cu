@@ -25,7 +25,6 @@ namespace gns {
 namespace {
 
 constexpr size_t kSmemTile = sizeof(SmemKV<TILE>);
-constexpr size_t kSmemTma = sizeof(MergeSmem<TMA_CHUNK>);
 template <int S>
 constexpr size_t ws_smem() { return sizeof(WsSmem<WS_CHUNK, S>); }
 template <int S>
@@ -120,9 +119,7 @@ void init_attributes()
 {
     std::call_once(g_attr_once, [] {
         set_smem(tile_sort_kernel<SORT_THREADS, SORT_ITEMS>, kSmemTile);
-        set_smem(merge_pass_tma_kernel<TMA_THREADS, TMA_ITEMS>, kSmemTma);
         set_smem(frog_setup_kernel<SORT_THREADS, SORT_ITEMS>, kSmemTile);
-        set_smem(frog_merge_tma_kernel<TMA_THREADS, TMA_ITEMS>, kSmemTma);
         set_smem(merge_pass_ws_kernel<2>, ws_smem_out<2>());
         set_smem(merge_pass_ws_kernel<3>, ws_smem_out<3>());
         set_smem(merge_pass_ws_kernel<4>, ws_smem_out<4>());
@@ -133,17 +130,15 @@ void init_attributes()
 }
 
 // Merge-level pipeline (GNS_MERGE_PIPE overrides the default):
-//   "tma"  every thread stages and merges (gns_merge_tma.cuh);
 //   "ws2", "ws3", "ws4"  warp-specialised with 2 / 3 / 4 stages
-//   (gns_merge_ws.cuh; default ws2: six CTAs per SM, measured fastest).
-enum MergePipe { PIPE_TMA = 0, PIPE_WS2, PIPE_WS3, PIPE_WS4 };
+//   (gns_merge_ws.cuh; default ws2: the most resident CTAs, measured fastest).
+enum MergePipe { PIPE_WS2 = 0, PIPE_WS3, PIPE_WS4 };
 
 int merge_pipe()
 {
     static const int v = [] {
         const char* e = getenv("GNS_MERGE_PIPE");
         if (!e) return (int)PIPE_WS2;
-        if (!strcmp(e, "tma")) return (int)PIPE_TMA;
         if (!strcmp(e, "ws3")) return (int)PIPE_WS3;
         if (!strcmp(e, "ws4")) return (int)PIPE_WS4;
         return (int)PIPE_WS2;
@@ -194,12 +189,7 @@ cudaError_t launch_plain_level(const uint64_t* sk, const uint32_t* sv, uint64_t*
     case PIPE_WS2: return launch_plain_level_ws<2>(GNS_PLAIN_ARGS);
     case PIPE_WS3: return launch_plain_level_ws<3>(GNS_PLAIN_ARGS);
     case PIPE_WS4: return launch_plain_level_ws<4>(GNS_PLAIN_ARGS);
-    default: {
-        const int64_t grid = imin(nblocks, (int64_t)num_sms() * TMA_CTAS_PER_SM);
-        return launch(K_MERGE_PASS, merge_pass_tma_kernel<TMA_THREADS, TMA_ITEMS>, dim3((unsigned)grid),
-                      dim3(TMA_THREADS), kSmemTma, s, sk, sv, dk, dv, n, w, nblocks, splits, mode, decode, call_err,
-                      limit, skip);
-    }
+    default: return launch_plain_level_ws<2>(GNS_PLAIN_ARGS);
     }
 #undef GNS_PLAIN_ARGS
 }
@@ -213,12 +203,7 @@ cudaError_t launch_frog_level(const Slots& sl, const FrogItem* items, int64_t to
     case PIPE_WS2: return launch_frog_level_ws<2>(GNS_FROG_ARGS);
     case PIPE_WS3: return launch_frog_level_ws<3>(GNS_FROG_ARGS);
     case PIPE_WS4: return launch_frog_level_ws<4>(GNS_FROG_ARGS);
-    default: {
-        const int64_t grid = imin(total, (int64_t)num_sms() * TMA_CTAS_PER_SM);
-        return launch(K_FROG_MERGE, frog_merge_tma_kernel<TMA_THREADS, TMA_ITEMS>, dim3((unsigned)grid),
-                      dim3(TMA_THREADS), kSmemTma, s, sl, items, total, mode, decode, ticket, loaded, epoch,
-                      call_err, limit, skip_ticket, skip);
-    }
+    default: return launch_frog_level_ws<2>(GNS_FROG_ARGS);
     }
 #undef GNS_FROG_ARGS
 }
