@@ -11,11 +11,12 @@
 //     consumers have written it (the stage's "done" mbarrier) and -- in the
 //     in-place level -- once every item that reads the elements under the
 //     chunk's output has published its "inputs loaded" flag;
-//   * publishes the in-place level's "inputs loaded" flags as stages land;
 //   * reuses a stage once its store has read it.
-// The consumers only merge: wait for a stage, split it by merge path (8
-// outputs per thread), merge serially in registers, and -- after a barrier,
-// since the stage is their input -- write the outputs back into the same stage,
+// The consumers merge: wait for a stage (in the in-place level the first
+// consumer thread then publishes the item's "inputs loaded" flag), split it by
+// merge path (8 outputs per thread), merge serially in registers, and -- after
+// a barrier, since the stage is their input -- write the outputs back into the
+// same stage,
 // placed so that shared and global addresses agree modulo 16 bytes (one bulk
 // store for the aligned interior, plain stores for at most 1 key / 3 payload
 // words at each end).  The consumers never wait on another CTA, and the
@@ -70,6 +71,7 @@ struct WsInfo {
     int shk, shv;                 // outputs start at shared index shk (keys) / shv (payload)
     int decode;
     int end;                      // no more items
+    int64_t tk;                   // in-place level: the item's "loaded" flag
 };
 
 // What the producer keeps of a staged item until its store.
@@ -329,34 +331,19 @@ __device__ __forceinline__ void ws_merge(Src& src, const Slots& sl, bool has_val
         // ------------------------------------------------------------ producer
         if (t != 0) return;
         WsOut out[S];
-        int64_t stk[S];
         int32_t sdn[S], sdh[S];
-        bool spub[S];
         int64_t n_staged = 0;    // items staged (item i uses stage i % S)
         int64_t n_stored = 0;    // items whose store has been issued (in item order)
         bool no_more = false;
         bool failed = false;
         uint64_t t_last = global_ns();
-        for (int q = 0; q < S; ++q) spub[q] = true;
         for (;;) {
             bool progress = false;
-            // publish the "inputs loaded" flags of stages that have landed
-            if (FLAGS) {
-                for (int64_t i = n_stored; i < n_staged; ++i) {
-                    const int q = (int)(i % S);
-                    if (!spub[q] && mbar_test(&full[q], (unsigned)(i / S) & 1u)) {
-                        if (stk[q] != skip_ticket) st_release(&loaded[stk[q]], epoch);
-                        spub[q] = true;
-                        progress = true;
-                    }
-                }
-            }
             // store merged chunks, in item order
             while (n_stored < n_staged) {
                 const int q = (int)(n_stored % S);
                 if (!mbar_test(&done[q], (unsigned)(n_stored / S) & 1u)) break;
                 if (FLAGS) {
-                    if (!spub[q]) break;
                     bool ok = true;
                     while (sdn[q] <= sdh[q]) {
                         if (ld_acquire(&loaded[sdn[q]]) != epoch) {
@@ -416,11 +403,10 @@ __device__ __forceinline__ void ws_merge(Src& src, const Slots& sl, bool has_val
                         inf.shv = o.shv;
                         inf.decode = L.decode;
                         inf.end = 0;
+                        inf.tk = L.tk;
                         info[q] = inf;
-                        stk[q] = L.tk;
                         sdn[q] = L.dep_lo;
                         sdh[q] = L.dep_hi;
-                        spub[q] = !FLAGS;
                         ++n_staged;
                         mbar_arrive_expect_tx(&full[q], bytes);   // the arrival: the phase ends when the bytes land
                     }
@@ -458,6 +444,9 @@ __device__ __forceinline__ void ws_merge(Src& src, const Slots& sl, bool has_val
             s_cfail = 1;
         }
         const WsInfo inf = info[s];
+        // publish the item's "inputs loaded" flag as soon as its stage has landed
+        // (a consumer thread has no global stores outstanding, so the release is cheap)
+        if (FLAGS && ct == 0 && ok && !inf.end && inf.tk != skip_ticket) st_release(&loaded[inf.tk], epoch);
         uint64_t k[ITEMS];
         uint32_t v[ITEMS];
         int m = 0;
