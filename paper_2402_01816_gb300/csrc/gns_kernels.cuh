@@ -25,9 +25,14 @@
 
 namespace gns {
 
-constexpr int SORT_THREADS = 256;
+// Tile sort: SORT_THREADS x SORT_ITEMS elements per CTA (GNS_SORT_THREADS may
+// be set at build time).
+#ifndef GNS_SORT_THREADS
+#define GNS_SORT_THREADS 512
+#endif
+constexpr int SORT_THREADS = GNS_SORT_THREADS;
 constexpr int SORT_ITEMS = 16;
-constexpr int TILE = SORT_THREADS * SORT_ITEMS;       // 4096 elements
+constexpr int TILE = SORT_THREADS * SORT_ITEMS;       // elements per tile (8192 by default)
 // Merge levels work in chunks of CHUNK outputs, MERGE_ITEMS per consumer
 // thread (gns_merge_ws.cuh); GNS_MERGE_CONSUMERS may be set at build time.
 #ifndef GNS_MERGE_CONSUMERS

@@ -34,7 +34,7 @@ namespace gns {
 
 namespace {
 
-constexpr int SEG_T = TILE;        // tile of the big class (4096)
+constexpr int SEG_T = 4096;        // tile of the big class (seg_tile_kernel<256, 16>)
 
 struct SegChunk {
     int64_t out0, a_src, b_src;    // absolute positions

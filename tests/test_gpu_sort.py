@@ -9,9 +9,10 @@ from tests.gpu_util import assert_bitexact, from_dev, need_gpu, to_dev_keys, to_
 
 pytestmark = pytest.mark.gpu
 
-TILE = 4096
-SIZES = [0, 1, 2, 3, 17, 255, TILE - 1, TILE, TILE + 1, 2 * TILE - 1, 2 * TILE + 1, 3 * TILE + 5,
-         5 * TILE, 7 * TILE + 3, 16 * TILE, 16 * TILE + 1, 33 * TILE + 77, (1 << 18) + 12345]
+TILE = 4096      # sizes around 4096 and 8192: the tile edges of the tile sorts (8192) and of the
+                 # segmented sort's big class (4096), and the merge chunks (2048)
+SIZES = [0, 1, 2, 3, 17, 255, TILE - 1, TILE, TILE + 1, 2 * TILE - 1, 2 * TILE, 2 * TILE + 1, 3 * TILE + 5,
+         4 * TILE + 1, 5 * TILE, 7 * TILE + 3, 16 * TILE, 16 * TILE + 1, 33 * TILE + 77, (1 << 18) + 12345]
 TIERS = [1.0, 0.5]
 
 
