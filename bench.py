@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--n", type=int, default=N_FULL, help="keys per sort (default 2^27)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--paper-patterns", action="store_true",
+                    help="add the paper's pattern suite on both tiers (ratios in the form of its Squidsort table)")
     ap.add_argument("--large", action="store_true",
                     help="add the 2^31-key 50%%-tier run (about 40 GB on the device, minutes of input generation)")
     ap.add_argument("--no-extras", action="store_true",
@@ -325,6 +327,48 @@ def large_low_memory(dev, n=1 << 31):
     return out
 
 
+def paper_patterns(dev, n=1 << 27):
+    """The paper's pattern suite (Methods and measurement section) on both
+    tiers: time, %RAM and tFootprint per pattern and tier, and the 50%/100%
+    ratios r(%RAM), r(runTime), r(tFootprint) -- the form of the paper's
+    Squidsort-vs-Knuthsort table (its numbers are CPU ratios, context only)."""
+    import torch
+    import paper_2402_01816_gb300 as g
+    from paper_2402_01816_gb300 import inputs
+    out = {"workload": f"paper patterns, {n} float64 keys + uint32 index payload, 100% and 50% buffer",
+           "patterns": {}}
+    pay = torch.arange(n, dtype=torch.int64, device=dev).to(torch.int32)
+    tot = {1.0: 0.0, 0.5: 0.0}
+    for pattern in inputs.PAPER_PATTERNS:
+        keys = torch.from_numpy(inputs.make_keys(pattern, n, seed=0)).to(dev)
+        kt, pt = torch.empty_like(keys), torch.empty_like(pay)
+
+        def restore():
+            kt.copy_(keys)
+            pt.copy_(pay)
+        row = {}
+        for bf in (1.0, 0.5):
+            restore()
+            g.gns_sort(kt, pt, buffer_fraction=bf)
+            t = _time_ms(lambda: g.gns_sort(kt, pt, buffer_fraction=bf), restore)
+            ram = 1.0 + g.gns_workspace_bytes(n, bf) / (12.0 * n)
+            row[f"{int(bf * 100)}%"] = {"ms": t, "gkeys_s": n / t / 1e6, "pct_ram": ram, "t_footprint_ms": ram * t}
+            tot[bf] += t
+        if g.gns_stream_status() != 0:
+            raise RuntimeError("device status error in paper_patterns")
+        a, b = row["100%"], row["50%"]
+        row["r_pct_ram"] = b["pct_ram"] / a["pct_ram"]
+        row["r_runtime"] = b["ms"] / a["ms"]
+        row["r_t_footprint"] = b["t_footprint_ms"] / a["t_footprint_ms"]
+        out["patterns"][pattern] = row
+        del keys, kt, pt
+        torch.cuda.empty_cache()
+    r_ram = (1.0 + g.gns_workspace_bytes(n, 0.5) / (12.0 * n)) / (1.0 + g.gns_workspace_bytes(n, 1.0) / (12.0 * n))
+    out["TOTAL"] = {"ms_100": tot[1.0], "ms_50": tot[0.5], "r_pct_ram": r_ram, "r_runtime": tot[0.5] / tot[1.0],
+                    "r_t_footprint": r_ram * tot[0.5] / tot[1.0]}
+    return out
+
+
 def cpu_baseline(n_sample=1 << 25):
     import oracle
     from paper_2402_01816_gb300 import inputs
@@ -504,6 +548,8 @@ def run_ours(args, ws, rank, local):
     if not args.no_extras and args.n == N_FULL:
         extras["learned_vs_plain"] = learned_vs_plain(dev)
         extras["batched_vs_plain"] = batched_vs_plain(dev)
+    if args.paper_patterns:
+        extras["paper_patterns"] = paper_patterns(dev, args.n)
     if args.large:
         extras["large_low_memory"] = large_low_memory(dev)
     if rank != 0:

@@ -200,6 +200,40 @@ __device__ __forceinline__ int merge_staged_ct(const InStage<C>& st, const Stage
     return cnt - diag < ITEMS ? cnt - diag : ITEMS;
 }
 
+// A chunk whose outputs all come from one run (one slice empty: presorted
+// stretches) is a copy: consumer thread ct takes outputs ct, ct + CT, ...
+// (striped, so a warp's accesses are consecutive words: no bank conflicts).
+template <int C, int ITEMS, int CT>
+__device__ __forceinline__ void copy_staged_striped(const InStage<C>& st, const StagedChunk& g, uint64_t (&k)[ITEMS],
+                                                    uint32_t (&v)[ITEMS], bool has_vals, int ct)
+{
+    const bool from_a = g.nb == 0;
+    const int bk = from_a ? g.ka : g.kb, bv = from_a ? g.va : g.vb, cnt = g.na + g.nb;
+#pragma unroll
+    for (int x = 0; x < ITEMS; ++x) {
+        const int e = ct + x * CT;
+        if (e < cnt) {
+            k[x] = st.k[bk + e];
+            if (has_vals) v[x] = st.v[bv + e];
+        }
+    }
+}
+
+template <int ITEMS, int CT>
+__device__ __forceinline__ void write_striped_shifted(uint64_t* ok, uint32_t* ov, int shk, int shv,
+                                                     const uint64_t (&k)[ITEMS], const uint32_t (&v)[ITEMS], int cnt,
+                                                     bool has_vals, int mode, int decode_out, int ct)
+{
+#pragma unroll
+    for (int x = 0; x < ITEMS; ++x) {
+        const int e = ct + x * CT;
+        if (e < cnt) {
+            ok[shk + e] = decode_out ? decode_key(k[x], mode) : k[x];
+            if (has_vals) ov[shv + e] = v[x];
+        }
+    }
+}
+
 // Thread ct's m outputs to keys ok[shk + 8 ct ...] and payload ov[shv + 8 ct ...]:
 // 16-byte stores where the shift allows, narrower ones otherwise.
 template <int ITEMS>
@@ -450,10 +484,17 @@ __device__ __forceinline__ void ws_merge(Src& src, const Slots& sl, bool has_val
         uint64_t k[ITEMS];
         uint32_t v[ITEMS];
         int m = 0;
-        if (ok && !inf.end) m = merge_staged_ct<C, ITEMS>(sm.in[s], inf.g, k, v, has_vals, ct);
+        const bool one = inf.g.na == 0 || inf.g.nb == 0;   // uniform: from the stage's record
+        if (ok && !inf.end) {
+            if (one) copy_staged_striped<C, ITEMS, CT>(sm.in[s], inf.g, k, v, has_vals, ct);
+            else m = merge_staged_ct<C, ITEMS>(sm.in[s], inf.g, k, v, has_vals, ct);
+        }
         named_bar_sync(1, CT);                       // every consumer is done reading the stage
         if (s_cfail || inf.end) break;               // uniform: written before the barrier
-        if (m > 0)
+        if (one)
+            write_striped_shifted<ITEMS, CT>(sm.in[s].k, sm.in[s].v, inf.shk, inf.shv, k, v, inf.g.na + inf.g.nb,
+                                             has_vals, mode, inf.decode, ct);
+        else if (m > 0)
             write_out_shifted<ITEMS>(sm.in[s].k, sm.in[s].v, inf.shk, inf.shv, k, v, m, has_vals, mode, inf.decode,
                                      ct);
         fence_proxy_async_shared();
@@ -573,12 +614,19 @@ __device__ __forceinline__ void ws_merge_out(Src& src, bool has_vals, int mode, 
         uint64_t k[ITEMS];
         uint32_t v[ITEMS];
         int m = 0;
-        if (ok && !inf.end) m = merge_staged_ct<C, ITEMS>(sm.in[s], inf.g, k, v, has_vals, ct);
+        const bool one = inf.g.na == 0 || inf.g.nb == 0;   // uniform: from the stage's record
+        if (ok && !inf.end) {
+            if (one) copy_staged_striped<C, ITEMS, CT>(sm.in[s], inf.g, k, v, has_vals, ct);
+            else m = merge_staged_ct<C, ITEMS>(sm.in[s], inf.g, k, v, has_vals, ct);
+        }
         if (ct == 0) bulk_wait_read_all();           // the previous store has read `out`
         named_bar_sync(1, CT);
         if (s_cfail || inf.end) break;               // uniform: written before the barrier
         if (ct == 0) mbar_arrive(&freeb[s]);          // every consumer is done with the stage
-        if (m > 0)
+        if (one)
+            write_striped_shifted<ITEMS, CT>(sm.out.k, sm.out.v, inf.shk, inf.shv, k, v, inf.g.na + inf.g.nb,
+                                             has_vals, mode, inf.decode, ct);
+        else if (m > 0)
             write_out_shifted<ITEMS>(sm.out.k, sm.out.v, inf.shk, inf.shv, k, v, m, has_vals, mode, inf.decode, ct);
         fence_proxy_async_shared();
         named_bar_sync(1, CT);
