@@ -18,6 +18,8 @@ The oracle itself is plain C (``gns_oracle.c``), compiled with gcc into
                        Frogsort0 and Frogsort1 sections).
 * ``frog_trace``    -- slot labels after each merge level, for the layout tables
                        of the Frogsort0 / Frogsort1 sections.
+* ``frogsort2``     -- Frogsort2 section: imbalanced split with inner fraction p
+                       and floor(p n) buffer.
 * ``segmented_sort``, ``final_position``, ``compare``.
 """
 from __future__ import annotations
@@ -75,6 +77,10 @@ def _load():
             lib.orc_frogsort.argtypes = [P, P, i64, i32, i32, i32, P]
             lib.orc_frogsort.restype = i32
             lib.orc_frog_buffer.argtypes = [i64]
+            lib.orc_frogsort2.argtypes = [P, P, i64, i32, i32, i64, i64, i64, P]
+            lib.orc_frogsort2.restype = i32
+            lib.orc_frog2_buffer.argtypes = [i64, i64, i64]
+            lib.orc_frog2_buffer.restype = i64
             lib.orc_frog_buffer.restype = i64
             lib.orc_frog_depth.argtypes = [i64, i32]
             lib.orc_frog_depth.restype = i32
@@ -146,6 +152,30 @@ def frogsort(keys: np.ndarray, payload: np.ndarray | None = None, order: int = A
         return keys, payload, {"setup_moves": int(ctr[0]), "merge_moves": int(ctr[1]),
                                "merge_compares": int(ctr[2])}
     return keys, payload
+
+
+def frogsort2(keys: np.ndarray, payload: np.ndarray | None = None, order: int = ASC, p_num: int = 1,
+              p_den: int = 4, leaf: int = 1, return_counters: bool = False):
+    """Paper's Frogsort2 with inner fraction p = p_num / p_den (<= 1/2), using
+    floor(p n) buffer slots; nodes of at most `leaf` elements are the base case."""
+    keys, payload = _prep(keys, payload)
+    ctr = np.zeros(3, dtype=np.int64)
+    rc = _load().orc_frogsort2(_ptr(keys), _ptr(payload), keys.size, _key_type(keys), order, p_num, p_den, leaf,
+                               _ptr(ctr))
+    if rc == -2:
+        raise ValueError("Frogsort2 needs 0 < p <= 1/2 and leaf >= 1")
+    if rc == -3:
+        raise AssertionError("Frogsort2 layout broke buffer >= inner child")
+    if rc:
+        raise MemoryError("oracle frogsort2: allocation failed")
+    if return_counters:
+        return keys, payload, {"setup_moves": int(ctr[0]), "merge_moves": int(ctr[1]),
+                               "merge_compares": int(ctr[2])}
+    return keys, payload
+
+
+def frog2_buffer(n: int, p_num: int, p_den: int) -> int:
+    return int(_load().orc_frog2_buffer(n, p_num, p_den))
 
 
 def frog_buffer(n: int) -> int:

@@ -421,6 +421,136 @@ int orc_frogsort(uint64_t* keys, uint32_t* payload, int64_t n, int key_type, int
     return 0;
 }
 
+/* ------------------------------------------------------------------------
+ * Frogsort2 (Frogsort2 section): symmetric merging with an imbalanced split.
+ * With inner fraction p (here p_num / p_den <= 1/2) the inner branch of a
+ * node of n elements holds floor(p n) of them, and the whole sort needs only
+ * floor(p n) buffer slots.  Reading (the section gives only "inner branch
+ * p%, p% buffer"):
+ *   root:   n elements, b = floor(p n) buffer slots;
+ *   split:  n_inner = floor(p n), n_outer = n - n_inner;
+ *           b_outer = floor(p n_outer), b_inner = b - b_outer;
+ *   leaves: nodes of at most `leaf` elements, stably sorted into their data
+ *           slots at setup (the base case), every other node merged as in
+ *           Frogsort1 (frog_merge above: inner end to outer end).
+ * By induction every node keeps b >= floor(p n) = n_inner (floor(x) -
+ * floor(y) >= floor(x - y)), which is what the in-place merge needs; the code
+ * checks it anyway.  With p = 1/2 and leaf = 1 the split is Frogsort1's.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t pn, pd;     /* p = pn / pd */
+    int64_t leaf;
+    int bad;            /* set if a node breaks b >= n_inner */
+} frog2_cfg;
+
+static int64_t frog2_floor_p(const frog2_cfg* c, int64_t n) { return (n * c->pn) / c->pd; }
+
+static void frog2_children(const frog2_cfg* c, const frog_node* p, frog_node* L, frog_node* R)
+{
+    int64_t n_inner = frog2_floor_p(c, p->n), n_outer = p->n - n_inner;
+    int64_t b_outer = frog2_floor_p(c, n_outer), b_inner = p->b - b_outer;
+    L->side = 0; R->side = 1;
+    L->depth = R->depth = p->depth + 1;
+    if (p->side == 0) { L->n = n_outer; L->b = b_outer; R->n = n_inner; R->b = b_inner; }
+    else              { L->n = n_inner; L->b = b_inner; R->n = n_outer; R->b = b_outer; }
+    L->r = p->r;            R->r = p->r + L->n + L->b;
+    L->s = p->s;            R->s = p->s + L->n;
+}
+
+static int frog2_is_leaf(const frog2_cfg* c, const frog_node* x)
+{
+    return x->n <= c->leaf || frog2_floor_p(c, x->n) == 0;
+}
+
+static void frog2_setup_dest(frog2_cfg* c, const frog_node* x, int64_t* dest)
+{
+    if (frog2_is_leaf(c, x)) {
+        for (int64_t e = 0; e < x->n; e++) dest[x->s + e] = frog_data_slot(x) + e;
+        return;
+    }
+    frog_node L, R;
+    frog2_children(c, x, &L, &R);
+    frog2_setup_dest(c, &L, dest);
+    frog2_setup_dest(c, &R, dest);
+}
+
+/* the base case: a stable insertion sort of a leaf's slots */
+static void frog2_sort_leaf(frog_run* f, const frog_node* x)
+{
+    int64_t a = frog_data_slot(x), z = a + x->n;
+    for (int64_t i = a + 1; i < z; i++) {
+        uint64_t k = f->k[i];
+        uint32_t v = f->p ? f->p[i] : 0;
+        int64_t j = i - 1;
+        while (j >= a) {
+            f->c.compares++;
+            if (ord_cmp(f->k[j], k, f->c.key_type, f->c.order) <= 0) break;
+            f->k[j + 1] = f->k[j];
+            if (f->p) f->p[j + 1] = f->p[j];
+            j--;
+        }
+        f->k[j + 1] = k;
+        if (f->p) f->p[j + 1] = v;
+    }
+}
+
+static void frog2_sort_rec(frog2_cfg* c, frog_run* f, const frog_node* x)
+{
+    if (frog2_is_leaf(c, x)) {
+        frog2_sort_leaf(f, x);
+        return;
+    }
+    frog_node L, R;
+    frog2_children(c, x, &L, &R);
+    if (x->b < (x->side == 0 ? R.n : L.n)) c->bad = 1;   /* the inner child must fit the buffer */
+    frog2_sort_rec(c, f, &L);
+    frog2_sort_rec(c, f, &R);
+    frog_merge(f, x, &L, &R);
+}
+
+/* Buffer slots Frogsort2 needs for n elements: floor(p n). */
+int64_t orc_frog2_buffer(int64_t n, int64_t p_num, int64_t p_den) { return (n * p_num) / p_den; }
+
+/* Sort in place using floor(p n) extra slots, p = p_num / p_den in (0, 1/2];
+ * leaf >= 1.  counters as orc_frogsort.  Returns 0, -1 (allocation), -2
+ * (bad arguments) or -3 (a node broke b >= n_inner: cannot happen). */
+int orc_frogsort2(uint64_t* keys, uint32_t* payload, int64_t n, int key_type, int order, int64_t p_num,
+                  int64_t p_den, int64_t leaf, int64_t* counters)
+{
+    if (p_num <= 0 || p_den <= 0 || 2 * p_num > p_den || leaf < 1) return -2;
+    frog2_cfg c = {p_num, p_den, leaf, 0};
+    int64_t setup_moves = 0;
+    frog_run f;
+    memset(&f, 0, sizeof(f));
+    f.c.key_type = key_type; f.c.order = order;
+    if (n >= 2) {
+        int64_t b = frog2_floor_p(&c, n), m = n + b;
+        f.k = (uint64_t*)malloc((size_t)m * sizeof(uint64_t));
+        f.p = payload ? (uint32_t*)malloc((size_t)m * sizeof(uint32_t)) : NULL;
+        int64_t* dest = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+        if (!f.k || (payload && !f.p) || !dest) { free(f.k); free(f.p); free(dest); return -1; }
+        memcpy(f.k, keys, (size_t)n * sizeof(uint64_t));
+        if (payload) memcpy(f.p, payload, (size_t)n * sizeof(uint32_t));
+        frog_node root;
+        root.n = n; root.b = b; root.r = 0; root.s = 0; root.side = 0; root.depth = 0;
+        frog2_setup_dest(&c, &root, dest);
+        for (int64_t e = n - 1; e >= 0; e--) {      /* dest >= source, increasing: top down */
+            if (dest[e] != e) {
+                f.k[dest[e]] = f.k[e];
+                if (payload) f.p[dest[e]] = f.p[e];
+                setup_moves++;
+            }
+        }
+        free(dest);
+        frog2_sort_rec(&c, &f, &root);
+        memcpy(keys, f.k, (size_t)n * sizeof(uint64_t));
+        if (payload) memcpy(payload, f.p, (size_t)n * sizeof(uint32_t));
+        free(f.k); free(f.p);
+    }
+    if (counters) { counters[0] = setup_moves; counters[1] = f.c.moves; counters[2] = f.c.compares; }
+    return c.bad ? -3 : 0;
+}
+
 /* Depth of the Frogsort tree for n elements (leaves are single elements). */
 static int frog_depth_rec(const frog_node* x, int g)
 {

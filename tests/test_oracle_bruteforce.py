@@ -36,6 +36,9 @@ SORTS = {
     "definition": lambda k, p, o: oracle.stable_sort(k, p, o),
     "knuthsort": lambda k, p, o: oracle.knuthsort(k, p, o),
     "frogsort1": lambda k, p, o: oracle.frogsort(k, p, o, split_unit=1),
+    "frogsort2_1/4": lambda k, p, o: oracle.frogsort2(k, p, o, p_num=1, p_den=4, leaf=1),
+    "frogsort2_1/3_leaf2": lambda k, p, o: oracle.frogsort2(k, p, o, p_num=1, p_den=3, leaf=2),
+    "frogsort2_1/8": lambda k, p, o: oracle.frogsort2(k, p, o, p_num=1, p_den=8, leaf=1),
 }
 
 
