@@ -67,7 +67,7 @@ enum { GNS_WS_SORT = 0, GNS_WS_LEARNED = 1 };
  * gns_sort -- stable in-place sort of n float64 keys with uint32 payloads.
  *
  * Method: divide & conquer mergesort ("Merging or partitioning?" chapter:
- * split & merge, most work in the merge phases).  Tiles of up to 4096
+ * split & merge, most work in the merge phases).  Tiles of up to 8192
  * elements are sorted in shared memory; then every merge level is one pass
  * over HBM, split evenly across CTAs by merge-path co-rank search (the
  * "Parallel" section's binary merge over any number of workers).  Before
@@ -84,7 +84,15 @@ enum { GNS_WS_SORT = 0, GNS_WS_LEARNED = 1 };
  *               the data, left branches data-left, right branches data-right,
  *               merges from the inner ends outward, in place.  Workspace ~ 6 n
  *               bytes.
- *   < 0.5, NaN  GNS_ERR_UNSUPPORTED (< 0.5) / GNS_ERR_INVALID (NaN, negative).
+ *   [1/64, 0.5) Frogsort2 ("Frogsort2" section): the same symmetric merging
+ *               with an imbalanced split, inner branch fraction p =
+ *               buffer_fraction (rounded to a multiple of 2^-16): a node of m
+ *               elements gives floor(p m) to its inner child, and the sort
+ *               needs floor(p n) buffer slots (workspace ~ 12 p n bytes).  The
+ *               tree is deeper, so the sort does more merge work for less
+ *               memory.  The tree is planned on the host and uploaded with a
+ *               pageable copy, so this tier cannot be captured in a graph.
+ *   < 1/64, NaN GNS_ERR_UNSUPPORTED (< 1/64) / GNS_ERR_INVALID (NaN, negative).
  *
  * Arguments: keys (device, n float64), payload (device, n uint32, or NULL),
  * n >= 0 (n == 0 and n == 1 are no-ops), order GNS_ASCENDING/GNS_DESCENDING.

@@ -222,7 +222,7 @@ static int check_sort_args(const void* keys, const uint32_t* payload, int64_t n,
         const char* p1 = p0 + (size_t)n * 4;
         if (p0 < k1 && k0 < p1) return GNS_ERR_INVALID;   // keys and payload overlap
     }
-    if (bf < 0.5) return GNS_ERR_UNSUPPORTED;
+    if (bf < 1.0 / 64) return GNS_ERR_UNSUPPORTED;   // below Frogsort2's smallest inner fraction
     return GNS_OK;
 }
 

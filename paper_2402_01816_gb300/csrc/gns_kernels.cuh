@@ -404,14 +404,41 @@ __global__ void __launch_bounds__(THREADS)
     }
 }
 
-// splits[k*nch + c] = co-rank (left-run elements) of output c*CHUNK of node k.
+// The chunks of a level's nodes are numbered node by node: node k's chunks
+// are [cstart[k], cstart[k+1]).  cstart == nullptr: every node has nch chunk
+// slots (the balanced Frogsort1 tree; slots past a node's end are empty).
+__device__ __forceinline__ void frog_locate(int64_t idx, const int64_t* __restrict__ cstart, int64_t nnodes,
+                                            int64_t nch, int64_t& k, int64_t& local, int64_t& base, int64_t& nchk)
+{
+    if (!cstart) {
+        k = idx / nch;
+        local = idx % nch;
+        base = k * nch;
+        nchk = nch;
+        return;
+    }
+    int64_t lo = 0, hi = nnodes - 1;                 // last k with cstart[k] <= idx
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (cstart[mid] <= idx) lo = mid;
+        else hi = mid - 1;
+    }
+    k = lo;
+    base = cstart[k];
+    local = idx - base;
+    nchk = cstart[k + 1] - base;
+}
+
+// splits[base(k) + c] = co-rank (left-run elements) of output c*CHUNK of node k.
 static __global__ void frog_partition_kernel(Slots sl, const FrogNode* __restrict__ level,
                                       const FrogNode* __restrict__ child, int64_t nnodes, int64_t nch,
-                                      int64_t* splits, const int* presorted)
+                                      const int64_t* __restrict__ cstart, int64_t total, int64_t* splits,
+                                      const int* presorted)
 {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nnodes * nch || skip_all(presorted)) return;
-    int64_t k = idx / nch, c = idx % nch;
+    if (idx >= total || skip_all(presorted)) return;
+    int64_t k, c, base, nchk;
+    frog_locate(idx, cstart, nnodes, nch, k, c, base, nchk);
     FrogNode x = level[k], L = child[2 * k], R = child[2 * k + 1];
     int64_t diag = imin64(c * CHUNK, x.n);
     int64_t ra = frog_data_slot(L), rb = frog_data_slot(R);

@@ -192,17 +192,19 @@ __device__ __forceinline__ int2 frog_dep_range(int64_t c, const FrogNode& x, con
 }
 
 // items[tk] for every ticket tk of a level (after the partition, before the
-// merge): ticket tk = k * nch + local is chunk c = nch - 1 - local of a
-// data-left node k and chunk c = local of a data-right one.
+// merge): ticket tk = base(k) + local (frog_locate) is chunk c = nchk - 1 -
+// local of a data-left node k and chunk c = local of a data-right one.
 static __global__ void frog_items_kernel(const FrogNode* __restrict__ level, const FrogNode* __restrict__ child,
-                                         int64_t nnodes, int64_t nch, const int64_t* __restrict__ splits,
+                                         int64_t nnodes, int64_t nch, const int64_t* __restrict__ cstart,
+                                         int64_t total, const int64_t* __restrict__ splits,
                                          FrogItem* __restrict__ items, int* call_err, const int* presorted)
 {
     const int64_t tk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tk >= nnodes * nch || skip_all(presorted)) return;
-    const int64_t k = tk / nch, local = tk % nch;
+    if (tk >= total || skip_all(presorted)) return;
+    int64_t k, local, base, nchk;
+    frog_locate(tk, cstart, nnodes, nch, k, local, base, nchk);
     const FrogNode x = level[k];
-    const int64_t c = x.side == 0 ? nch - 1 - local : local;
+    const int64_t c = x.side == 0 ? nchk - 1 - local : local;
     FrogItem it;
     it.ra = it.rb = it.oslot = 0;
     it.na = it.nb = 0;
@@ -212,7 +214,7 @@ static __global__ void frog_items_kernel(const FrogNode* __restrict__ level, con
     if (w0 < x.n) {
         const int64_t w1 = imin64(w0 + CHUNK, x.n);
         const FrogNode L = child[2 * k], R = child[2 * k + 1];
-        const int64_t* sp = splits + k * nch;
+        const int64_t* sp = splits + base;
         const int64_t a0 = sp[c];
         const int64_t a1 = (w1 == x.n) ? L.n : sp[c + 1];
         const int64_t na = a1 - a0, nb = (w1 - a1) - (w0 - a0);
@@ -226,9 +228,8 @@ static __global__ void frog_items_kernel(const FrogNode* __restrict__ level, con
             it.oslot = frog_data_slot(x) + w0;
             const int2 r = frog_dep_range(c, x, L, R, sp, CHUNK);
             if (r.x <= r.y) {
-                const int64_t base = k * nch;
-                it.dep_lo = (int32_t)(x.side == 0 ? base + nch - 1 - r.y : base + r.x);
-                it.dep_hi = (int32_t)(x.side == 0 ? base + nch - 1 - r.x : base + r.y);
+                it.dep_lo = (int32_t)(x.side == 0 ? base + nchk - 1 - r.y : base + r.x);
+                it.dep_hi = (int32_t)(x.side == 0 ? base + nchk - 1 - r.x : base + r.y);
             }
         }
     }

@@ -8,12 +8,18 @@
 //   50% tier  : node plan -> fused setup (tile sort + scatter into the gapped
 //               Frogsort1 leaf slots) -> one in-place merge level per tree depth
 //               ("Symmetric merging", "Frogsort1").
+//   < 50% tier: the same with Frogsort2's imbalanced tree (inner fraction p =
+//               buffer_fraction, floor(p n) buffer; "Frogsort2"), planned on the
+//               host: nodes of very different sizes share a depth, so each
+//               depth gets its own node list and chunk numbering.
 // Keys are encoded (order map) when first read and decoded by the last write.
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "gns_internal.h"
 #include "gns_kernels.cuh"
@@ -66,6 +72,138 @@ int frog_leaf_depth(int64_t n)
 
 int64_t frog_chunks(int64_t n, int d) { return ceil_div(ceil_div(n, 1ll << d), CHUNK); }
 
+// Frogsort2 inner fraction p = pn / FROG2_DEN for buffer_fraction < 1/2.
+constexpr int64_t FROG2_DEN = 1 << 16;
+int64_t frog2_num(double bf) { return (int64_t)(bf * (double)FROG2_DEN + 0.5); }
+
+// Frogsort2 split (Frogsort2 section): the inner child gets floor(p n) elements,
+// the outer child floor(p n_outer) buffer slots and the inner child the rest of
+// the node's buffer, so every node keeps at least floor(p n) = n_inner slots.
+void frog2_split(const FrogNode& p, int64_t pn, FrogNode& L, FrogNode& R)
+{
+    const int64_t n_inner = p.n * pn / FROG2_DEN, n_outer = p.n - n_inner;
+    const int64_t b_outer = n_outer * pn / FROG2_DEN, b_inner = p.b - b_outer;
+    if (p.side == 0) { L.n = n_outer; L.b = b_outer; R.n = n_inner; R.b = b_inner; }
+    else             { L.n = n_inner; L.b = b_inner; R.n = n_outer; R.b = b_outer; }
+    L.side = 0; R.side = 1; L.pad = R.pad = 0;
+    L.r = p.r; R.r = p.r + L.n + L.b;
+    L.s = p.s; R.s = p.s + L.n;
+}
+
+// The Frogsort2 tree, depth by depth (nodes of at most TILE elements are
+// leaves, sorted at setup).  Depth d's internal nodes are
+// internal[first_node[d], first_node[d+1]), their children pairs follow the
+// same order in `children`, and their chunks are numbered by
+// cstart[first_cs[d] + k] (k-th node of the depth) up to cstart[first_cs[d] + nk].
+struct Frog2Plan {
+    std::vector<FrogNode> internal, children, leaves;
+    std::vector<int64_t> cstart, first_node, first_cs;
+    int64_t max_items = 0;
+    int D = 0;
+};
+
+Frog2Plan frog2_plan(int64_t n, int64_t pn)
+{
+    Frog2Plan P;
+    std::vector<FrogNode> cur(1), nxt;
+    cur[0].n = n; cur[0].b = n * pn / FROG2_DEN; cur[0].r = 0; cur[0].s = 0; cur[0].side = 0; cur[0].pad = 0;
+    while (!cur.empty()) {
+        nxt.clear();
+        const int64_t first = (int64_t)P.internal.size(), first_c = (int64_t)P.cstart.size();
+        int64_t acc = 0;
+        for (const FrogNode& x : cur) {
+            if (x.n <= TILE) {
+                P.leaves.push_back(x);
+                continue;
+            }
+            FrogNode L, R;
+            frog2_split(x, pn, L, R);
+            P.internal.push_back(x);
+            P.children.push_back(L);
+            P.children.push_back(R);
+            P.cstart.push_back(acc);
+            acc += ceil_div(x.n, CHUNK);
+            nxt.push_back(L);
+            nxt.push_back(R);
+        }
+        if ((int64_t)P.internal.size() == first) break;
+        P.cstart.push_back(acc);
+        P.first_node.push_back(first);
+        P.first_cs.push_back(first_c);
+        P.max_items = acc > P.max_items ? acc : P.max_items;
+        ++P.D;
+        cur.swap(nxt);
+    }
+    P.first_node.push_back((int64_t)P.internal.size());
+    std::sort(P.leaves.begin(), P.leaves.end(), [](const FrogNode& a, const FrogNode& b) { return a.s < b.s; });
+    return P;
+}
+
+// Frogsort2 plans, uploaded once per (device, n, p) and kept: the host work
+// (building the tree) and the upload would otherwise idle the GPU on every
+// call.  A handful of shapes are kept; an evicted plan's device copy is freed
+// after the device has finished every call that may still read it.
+struct Frog2Dev {
+    int dev = -1;
+    int64_t n = 0, pn = 0;
+    Frog2Plan plan;               // host copy: per-depth offsets and totals
+    char* d = nullptr;            // internal | children | leaves | cstart
+    size_t o_ch = 0, o_lv = 0, o_cs = 0;
+    uint64_t used = 0;
+};
+std::mutex g_frog2_mu;
+std::vector<Frog2Dev> g_frog2;
+uint64_t g_frog2_clock = 0;
+constexpr size_t kFrog2Cache = 4;
+
+// Returns the cached plan for (current device, n, pn), uploading it if new;
+// nullptr on a CUDA error.  The caller holds g_frog2_mu.
+const Frog2Dev* frog2_get(int64_t n, int64_t pn)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    for (Frog2Dev& e : g_frog2)
+        if (e.dev == dev && e.n == n && e.pn == pn) {
+            e.used = ++g_frog2_clock;
+            return &e;
+        }
+    Frog2Dev e;
+    e.dev = dev; e.n = n; e.pn = pn;
+    e.plan = frog2_plan(n, pn);
+    const Frog2Plan& P = e.plan;
+    e.o_ch = P.internal.size() * sizeof(FrogNode);
+    e.o_lv = e.o_ch + P.children.size() * sizeof(FrogNode);
+    e.o_cs = e.o_lv + P.leaves.size() * sizeof(FrogNode);
+    const size_t bytes = e.o_cs + P.cstart.size() * sizeof(int64_t);
+    std::vector<char> blob(bytes);
+    if (!P.internal.empty()) memcpy(blob.data(), P.internal.data(), e.o_ch);
+    if (!P.children.empty()) memcpy(blob.data() + e.o_ch, P.children.data(), e.o_lv - e.o_ch);
+    if (!P.leaves.empty()) memcpy(blob.data() + e.o_lv, P.leaves.data(), e.o_cs - e.o_lv);
+    if (!P.cstart.empty()) memcpy(blob.data() + e.o_cs, P.cstart.data(), bytes - e.o_cs);
+    if (cudaMalloc(&e.d, bytes ? bytes : 16) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (cudaMemcpy(e.d, blob.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(e.d);
+        return nullptr;
+    }
+    e.used = ++g_frog2_clock;
+    if (g_frog2.size() >= kFrog2Cache) {
+        size_t v = 0;
+        for (size_t i = 1; i < g_frog2.size(); ++i)
+            if (g_frog2[i].used < g_frog2[v].used) v = i;
+        int cur = dev;
+        cudaSetDevice(g_frog2[v].dev);
+        cudaDeviceSynchronize();                     // no call still reads the evicted plan
+        cudaFree(g_frog2[v].d);
+        cudaSetDevice(cur);
+        g_frog2.erase(g_frog2.begin() + (long)v);
+    }
+    g_frog2.push_back(std::move(e));
+    return &g_frog2.back();
+}
+
 struct Layout {
     // control words (ints): [0..1] presorted flags, [2] call error
     size_t ctl, bufk, bufv, splits, items, nodes, flags, tickets, total;
@@ -73,13 +211,23 @@ struct Layout {
     int L, D;
 };
 
-Layout make_layout(int64_t n, double bf, bool with_vals)
+Layout make_layout(int64_t n, double bf, bool with_vals, const Frog2Plan* plan)
 {
     Layout o{};
     size_t off = 0;
     o.ctl = off; off += 256;
     if (n <= TILE) { o.total = off; return o; }
-    if (bf >= 1.0) {
+    if (bf < 0.5 && plan) {
+        const int64_t b = n * frog2_num(bf) / FROG2_DEN;
+        o.D = plan->D;
+        o.bufk = off; off += align256((size_t)b * 8);
+        o.bufv = off; off += with_vals ? align256((size_t)b * 4) : 0;
+        o.splits = off; off += align256((size_t)plan->max_items * 8);
+        o.items = off; off += align256((size_t)plan->max_items * sizeof(FrogItem));
+        o.flags = off; o.flags_bytes = align256((plan->leaves.size() + (size_t)plan->max_items) * 4);
+        off += o.flags_bytes;
+        o.tickets = off; o.tickets_bytes = align256((size_t)(plan->D + 2) * 4); off += o.tickets_bytes;
+    } else if (bf >= 1.0) {
         o.L = merge_levels(n);
         int64_t nblocks = ceil_div(n, CHUNK);
         o.bufk = off; off += align256((size_t)n * 8);
@@ -229,13 +377,28 @@ cudaError_t publish_call_error(const int* call_err, cudaStream_t s)
 size_t sort_workspace_bytes(int64_t n, double bf)
 {
     if (n <= 1) return 0;
-    return make_layout(n, bf, true).total;
+    if (bf < 0.5 && n > TILE) {
+        const Frog2Plan plan = frog2_plan(n, frog2_num(bf));
+        // the plan itself is kept by the library (frog2_get), apart from the workspace
+        const size_t plan_bytes = (plan.internal.size() + plan.children.size() + plan.leaves.size()) *
+                                      sizeof(FrogNode) + plan.cstart.size() * sizeof(int64_t);
+        return make_layout(n, bf, true, &plan).total + align256(plan_bytes);
+    }
+    return make_layout(n, bf, true, nullptr).total;
 }
 
 int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, cudaStream_t s)
 {
     if (n <= 1) return GNS_OK;
-    const Layout lay = make_layout(n, bf, vals != nullptr);
+    const bool frog2 = bf < 0.5 && n > TILE;
+    std::unique_lock<std::mutex> plan_lock(g_frog2_mu, std::defer_lock);
+    const Frog2Dev* fp = nullptr;
+    if (frog2) {
+        plan_lock.lock();                            // held for the call: the entry may not be evicted
+        fp = frog2_get(n, frog2_num(bf));
+        if (!fp) return GNS_ERR_CUDA;
+    }
+    const Layout lay = make_layout(n, bf, vals != nullptr, frog2 ? &fp->plan : nullptr);
     char* ws = (char*)ws_alloc(lay.total, s);
     if (!ws) return GNS_ERR_OOM;
     init_attributes();
@@ -255,6 +418,44 @@ int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, 
     if (n <= TILE) {
         GNS_TRY(launch(K_TILE_SORT, tile_sort_kernel<SORT_THREADS, SORT_ITEMS>, dim3(1), dim3(SORT_THREADS),
                        kSmemTile, s, (const uint64_t*)keys, (const uint32_t*)vals, keys, vals, n, mode, 1, skip));
+    } else if (frog2) {
+        const int D = lay.D;
+        Slots sl;
+        sl.k0 = keys; sl.v0 = vals; sl.n = n; sl.b = n * frog2_num(bf) / FROG2_DEN;
+        sl.k1 = (uint64_t*)(ws + lay.bufk);
+        sl.v1 = vals ? (uint32_t*)(ws + lay.bufv) : nullptr;
+        const Frog2Plan& plan = fp->plan;
+        const FrogNode* internal = (const FrogNode*)fp->d;
+        const FrogNode* children = (const FrogNode*)(fp->d + fp->o_ch);
+        const FrogNode* leaves = (const FrogNode*)(fp->d + fp->o_lv);
+        const int64_t* cstart = (const int64_t*)(fp->d + fp->o_cs);
+        int64_t* splits = (int64_t*)(ws + lay.splits);
+        FrogItem* items = (FrogItem*)(ws + lay.items);
+        int* flags = (int*)(ws + lay.flags);
+        int* tickets = (int*)(ws + lay.tickets);
+        const uint64_t limit = wait_limit_ns();
+        GNS_TRY(cudaMemsetAsync(flags, 0, lay.flags_bytes + lay.tickets_bytes, s));
+        const int64_t nleaves = (int64_t)plan.leaves.size();
+        GNS_TRY(launch(K_FROG_SETUP, frog_setup_kernel<SORT_THREADS, SORT_ITEMS>, dim3((unsigned)nleaves),
+                       dim3(SORT_THREADS), kSmemTile, s, sl, leaves, nleaves, mode, tickets + D, flags, call_err,
+                       limit, skip));
+        int* lflags = flags + nleaves;
+        int64_t skip_ticket = take_debug_skip_publish();
+        for (int d = D - 1; d >= 0; --d) {
+            const int64_t f0 = plan.first_node[d], nnodes = plan.first_node[d + 1] - f0;
+            const int64_t c0 = plan.first_cs[d], total = plan.cstart[c0 + nnodes];
+            const FrogNode* level = internal + f0;
+            const FrogNode* child = children + 2 * f0;
+            const int64_t* cs = cstart + c0;
+            GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel, dim3((unsigned)ceil_div(total, 256)), dim3(256), 0,
+                           s, sl, level, child, nnodes, (int64_t)0, cs, total, splits, skip));
+            GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel, dim3((unsigned)ceil_div(total, 256)), dim3(256), 0, s,
+                           level, child, nnodes, (int64_t)0, cs, total, (const int64_t*)splits, items, call_err,
+                           skip));
+            GNS_TRY(launch_frog_level(sl, (const FrogItem*)items, total, mode, (int)(d == 0), tickets + d, lflags,
+                                      D - d, call_err, limit, skip_ticket, skip, s));
+            skip_ticket = -1;
+        }
     } else if (bf >= 1.0) {
         const int L = lay.L;
         uint64_t* bufk = (uint64_t*)(ws + lay.bufk);
@@ -308,10 +509,11 @@ int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, 
             const FrogNode* level = nodes + (nnodes - 1);
             const FrogNode* child = nodes + (2 * nnodes - 1);
             GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel, dim3((unsigned)ceil_div(nnodes * nch, 256)),
-                           dim3(256), 0, s, sl, level, child, nnodes, nch, splits, skip));
+                           dim3(256), 0, s, sl, level, child, nnodes, nch, (const int64_t*)nullptr, nnodes * nch,
+                           splits, skip));
             GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel, dim3((unsigned)ceil_div(nnodes * nch, 256)),
-                           dim3(256), 0, s, level, child, nnodes, nch, (const int64_t*)splits, items, call_err,
-                           skip));
+                           dim3(256), 0, s, level, child, nnodes, nch, (const int64_t*)nullptr, nnodes * nch,
+                           (const int64_t*)splits, items, call_err, skip));
             GNS_TRY(launch_frog_level(sl, (const FrogItem*)items, nnodes * nch, mode, (int)(d == 0), tickets + d,
                                       lflags, D - d, call_err, limit, skip_ticket, skip, s));
             skip_ticket = -1;

@@ -53,7 +53,7 @@ FAKE = 1 << 40   # a device-looking address; validation fails before any use
     ((FAKE, None, 10, 2, 1.0), -1),            # unknown order
     ((FAKE, None, 10, 0, math.nan), -1),       # NaN buffer fraction
     ((FAKE, None, 10, 0, -0.5), -1),           # negative buffer fraction
-    ((FAKE, None, 10, 0, 0.3), -2),            # below the 50% tier
+    ((FAKE, None, 10, 0, 0.01), -2),           # below the smallest Frogsort2 inner fraction (1/64)
     ((FAKE + 4, None, 10, 0, 1.0), -1),        # keys not 8-byte aligned
     ((FAKE, FAKE + 2, 10, 0, 1.0), -1),        # payload misaligned
     ((FAKE, FAKE + 40, 10, 0, 1.0), -1),       # keys and payload overlap
@@ -98,6 +98,10 @@ def test_workspace_bytes_match_tiers(L):
     ram_half = (12 * n + half) / (12 * n)
     assert 2.0 <= ram_full < 2.01
     assert 1.5 <= ram_half < 1.51
+    # Frogsort2: floor(p n) buffer slots (Frogsort2 section)
+    for p in (0.25, 0.1):
+        ram = (12 * n + L.gns_workspace_bytes(n, p, 0)) / (12 * n)
+        assert 1 + p <= ram < 1 + p + 0.01, (p, ram)
     assert L.gns_workspace_bytes(1, 1.0, 0) == 0
     assert L.gns_workspace_bytes(4096, 1.0, 0) <= 4096
 

@@ -137,3 +137,31 @@ def test_workspace_matches_tier_ram():
     n = 1 << 22
     assert g.gns_workspace_bytes(n, 1.0) >= 12 * n
     assert 6 * n <= g.gns_workspace_bytes(n, 0.5) < 6.1 * n
+
+
+FROG2_P = [0.25, 0.1, 0.4, 1.0 / 64]
+
+
+@pytest.mark.parametrize("p", FROG2_P)
+@pytest.mark.parametrize("n", [2 * TILE + 1, 5 * TILE + 3, 37 * TILE + 11, (1 << 18) + 12345])
+def test_frogsort2_sizes(n, p):
+    """Frogsort2 tier (buffer_fraction < 1/2): bit-exact stable sort."""
+    need_gpu()
+    _run(inputs.make_keys("ties", n, seed=n), 0, p)
+
+
+@pytest.mark.parametrize("p", [0.25, 0.1])
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("pattern", ["permut", "asc_noise", "tielog2", "descglobal", "mixture"])
+def test_frogsort2_patterns(pattern, order, p):
+    need_gpu()
+    _run(inputs.make_keys(pattern, 70 * TILE + 1234, seed=5), order, p)
+
+
+def test_frogsort2_workspace_is_p_of_data():
+    need_gpu()
+    import paper_2402_01816_gb300 as g
+    n = 1 << 22
+    for p in (0.25, 0.1):
+        ws = g.gns_workspace_bytes(n, p)
+        assert 12 * p * n <= ws < 12 * p * n + 0.1 * n     # %RAM = 1 + p + under 1%
