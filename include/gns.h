@@ -179,11 +179,12 @@ int gns_sort_noalloc(double* keys, uint32_t* payload, int64_t n, int order,
  * of the input (synchronising the stream) and keeps the fastest; the call then
  * captures its whole kernel sequence into a CUDA graph, cached with its
  * workspace for these pointers (up to four graphs; the oldest is released).
- * Later calls replay the graph.  Set GNS_SEG_SCHEDULE=0|1|2 to skip tuning.
+ * Later calls replay the graph.  Set GNS_SEG_SCHEDULE=0..4 to skip tuning.
  *   gns_segmented_schedule: index of the tuned schedule for this shape
  *     (0 = one 4096-key tile shape for every segment, 1 = segments of up to 1024
- *     keys sorted by 64-thread CTAs, 2 = up to 2048 keys by 128-thread CTAs),
- *     or -1 if none was tuned yet.
+ *     keys sorted by 64-thread CTAs, 2 = up to 2048 keys by 128-thread CTAs,
+ *     3 and 4 = schedules 0 and 2 with 8192-key tiles by 512-thread CTAs for
+ *     the other segments), or -1 if none was tuned yet.
  *   gns_segmented_release: synchronises `stream`, destroys the cached graphs and
  *     frees their workspace, and forgets the tuned schedules.
  */

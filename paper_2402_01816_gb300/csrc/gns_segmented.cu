@@ -34,7 +34,7 @@ namespace gns {
 
 namespace {
 
-constexpr int SEG_T = 4096;        // tile of the big class (seg_tile_kernel<256, 16>)
+constexpr int SEG_T_MIN = 4096;    // smallest big-class tile (seg_tile_kernel<256, 16>); 8192 with <512, 16>
 
 struct SegChunk {
     int64_t out0, a_src, b_src;    // absolute positions
@@ -49,13 +49,14 @@ struct SegChunk {
 // skip (optional): segments flagged non-zero are left as they are (already in
 // order, e.g. all keys equal) and get no work.
 __global__ void seg_count_kernel(const int64_t* __restrict__ off, int64_t nseg, int L, int64_t small_max,
-                                 int64_t* rows, uint8_t* levels, const uint8_t* __restrict__ skip, const int* ctl)
+                                 int64_t big_t, int64_t* rows, uint8_t* levels, const uint8_t* __restrict__ skip,
+                                 const int* ctl)
 {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nseg || skip_all(ctl)) return;
     const int64_t stride = nseg + 1;
     const int64_t len = (skip && skip[s]) ? 0 : off[s + 1] - off[s];
-    const int64_t tiles = (len + SEG_T - 1) / SEG_T;
+    const int64_t tiles = (len + big_t - 1) / big_t;
     int k = 0;
     while ((1ll << k) < tiles) ++k;
     levels[s] = (uint8_t)k;
@@ -175,7 +176,8 @@ __global__ void __launch_bounds__(THREADS)
 // merge-path splits, written to list[i].
 __global__ void seg_partition_kernel(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ bufk,
                                      const int64_t* __restrict__ off, int64_t nseg, const int64_t* __restrict__ prefix,
-                                     const uint8_t* __restrict__ levels, int p, SegChunk* list, const int* ctl)
+                                     const uint8_t* __restrict__ levels, int p, int64_t big_t, SegChunk* list,
+                                     const int* ctl)
 {
     if (skip_all(ctl)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -186,7 +188,7 @@ __global__ void seg_partition_kernel(const uint64_t* __restrict__ keys, const ui
     const int k = levels[s];
     const int from_buf = (k - p) & 1;
     const uint64_t* src = (from_buf ? bufk : keys) + seg0;
-    const int64_t w = (int64_t)SEG_T << p;
+    const int64_t w = big_t << p;
     const int64_t o = c * CHUNK;
     const int64_t ps = (o / (2 * w)) * (2 * w);
     const int64_t lenA = imin64(w, len - ps), lenB = imax64(0, imin64(w, len - ps - w));
@@ -267,16 +269,21 @@ int num_sms_dev()
     return v > 0 ? v : 152;
 }
 
-// Schedules the autotuner chooses from: small-class bound and its CTA shape.
+// Schedules the autotuner chooses from: small-class bound and its CTA shape,
+// and the big class's tile (4096 keys by 256 threads or 8192 by 512).
 struct SegSchedule {
     int64_t small_max;   // 0: no small class
     int small_threads;   // 64 (x16 = 1024 keys) or 128 (x16 = 2048 keys)
+    int big_t;           // 4096 or 8192
 };
-const SegSchedule kCandidates[] = {{0, 0}, {1024, 64}, {2048, 128}};
+const SegSchedule kCandidates[] = {{0, 0, 4096}, {1024, 64, 4096}, {2048, 128, 4096}, {0, 0, 8192},
+                                   {2048, 128, 8192}};
+// The learned path's buckets (tens of thousands of keys each): big tiles only.
+const SegSchedule kDirect = {0, 0, 8192};
 
 int max_levels(int64_t n)
 {
-    int64_t tiles = ceil_div(n, SEG_T);
+    int64_t tiles = ceil_div(n, SEG_T_MIN);
     int L = 0;
     while ((1ll << L) < tiles) ++L;
     return L;
@@ -310,6 +317,8 @@ void seg_init_attributes()
     std::call_once(g_seg_attr_once, [] {
         cudaFuncSetAttribute(seg_tile_kernel<256, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(SmemKV<4096>));
+        cudaFuncSetAttribute(seg_tile_kernel<512, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(SmemKV<8192>));
         cudaFuncSetAttribute(seg_tile_kernel<128, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(SmemKV<2048>));
         cudaFuncSetAttribute(seg_tile_kernel<64, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -336,7 +345,7 @@ cudaError_t seg_enqueue(uint64_t* keys, uint32_t* vals, const int64_t* off, int6
     cudaError_t e = cudaMemsetAsync(ctl, 0, 256, s);
     if (e != cudaSuccess) return e;
     e = launch(K_SEG_PLAN, seg_count_kernel, dim3((unsigned)ceil_div(nseg, 256)), dim3(256), 0, s, off, nseg, lay.L,
-               sch.small_max, rows, levels, skip, (const int*)ctl);
+               sch.small_max, (int64_t)sch.big_t, rows, levels, skip, (const int*)ctl);
     if (e != cudaSuccess) return e;
     e = launch(K_SEG_PLAN, seg_scan_kernel, dim3((unsigned)(2 + lay.L)), dim3(1024), 0, s, rows, nseg,
                (const int*)ctl);
@@ -352,15 +361,20 @@ cudaError_t seg_enqueue(uint64_t* keys, uint32_t* vals, const int64_t* off, int6
                        (const uint8_t*)levels, mode, (const int*)ctl);
         if (e != cudaSuccess) return e;
     }
-    e = launch(K_SEG_TILE, seg_tile_kernel<256, 16>, dim3((unsigned)(sms * 4)), dim3(256), sizeof(SmemKV<4096>), s,
-               keys, vals, bufk, bufv, off, nseg, (const int64_t*)(rows + stride), (const uint8_t*)levels, mode,
-               (const int*)ctl);
+    if (sch.big_t == 8192)
+        e = launch(K_SEG_TILE, seg_tile_kernel<512, 16>, dim3((unsigned)(sms * 2)), dim3(512), sizeof(SmemKV<8192>),
+                   s, keys, vals, bufk, bufv, off, nseg, (const int64_t*)(rows + stride), (const uint8_t*)levels, mode,
+                   (const int*)ctl);
+    else
+        e = launch(K_SEG_TILE, seg_tile_kernel<256, 16>, dim3((unsigned)(sms * 4)), dim3(256), sizeof(SmemKV<4096>),
+                   s, keys, vals, bufk, bufv, off, nseg, (const int64_t*)(rows + stride), (const uint8_t*)levels, mode,
+                   (const int*)ctl);
     if (e != cudaSuccess) return e;
     for (int p = 0; p < lay.L; ++p) {
         const int64_t* prefix = rows + (2 + p) * stride;
         e = launch(K_SEG_MERGE, seg_partition_kernel, dim3((unsigned)ceil_div(lay.max_items, 256)), dim3(256), 0, s,
-                   (const uint64_t*)keys, (const uint64_t*)bufk, off, nseg, prefix, (const uint8_t*)levels, p, list,
-                   (const int*)ctl);
+                   (const uint64_t*)keys, (const uint64_t*)bufk, off, nseg, prefix, (const uint8_t*)levels, p,
+                   (int64_t)sch.big_t, list, (const int*)ctl);
         if (e != cudaSuccess) return e;
         const int64_t cap = (int64_t)sms * ws_ctas_per_sm<SEG_WS_STAGES>();
         const int64_t grid = lay.max_items < cap ? lay.max_items : cap;
@@ -474,7 +488,7 @@ int segmented_sort_device(uint64_t* keys, uint32_t* vals, const int64_t* off, in
         const char* fixed = getenv("GNS_SEG_SCHEDULE");
         if (fixed) {
             sched = atoi(fixed);
-            if (sched < 0 || sched > 2) sched = 0;
+            if (sched < 0 || sched >= (int)(sizeof(kCandidates) / sizeof(kCandidates[0]))) sched = 0;
         } else {
             int rc = GNS_OK;
             sched = autotune(keys, vals, off, nseg, n, mode, s, &rc);
@@ -549,7 +563,7 @@ int segmented_sort_direct(uint64_t* keys, uint32_t* vals, const int64_t* off, in
     const SegLayout lay = seg_layout(n, nseg, vals != nullptr);
     char* ws = (char*)ws_alloc(lay.total, s);
     if (!ws) return GNS_ERR_OOM;
-    cudaError_t e = seg_enqueue(keys, vals, off, nseg, n, mode, kCandidates[0], ws, lay, s, skip);
+    cudaError_t e = seg_enqueue(keys, vals, off, nseg, n, mode, kDirect, ws, lay, s, skip);
     ws_free(ws, s);
     return e == cudaSuccess ? GNS_OK : GNS_ERR_CUDA;
 }

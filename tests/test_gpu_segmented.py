@@ -48,13 +48,14 @@ def _run(keys, off, order=0, with_payload=True, schedule=None, repeat=1):
 
 LENGTH_SETS = {
     "tiny_and_empty": [0, 1, 2, 0, 3, 16, 0, 17, 31, 1, 0],
-    "tile_edges": [TILE - 1, TILE, TILE + 1, 2 * TILE, 2 * TILE + 1, 1023, 1024, 1025, 2047, 2048, 2049],
+    "tile_edges": [TILE - 1, TILE, TILE + 1, 2 * TILE - 1, 2 * TILE, 2 * TILE + 1, 1023, 1024, 1025, 2047, 2048,
+                   2049, 4 * TILE + 1],
     "multi_level": [5 * TILE + 7, 33 * TILE + 1, 2, (1 << 17) + 3, 100, 9 * TILE],
     "one_big": [(1 << 19) + 5],
 }
 
 
-@pytest.mark.parametrize("schedule", [0, 1, 2])
+@pytest.mark.parametrize("schedule", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("name", sorted(LENGTH_SETS))
 def test_length_sets_int64(name, schedule):
     need_gpu()
