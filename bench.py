@@ -385,6 +385,19 @@ def cpu_baseline(n_sample=1 << 25):
                       f"({keys} keys, {t:.1f} s)"}
 
 
+def aggregate_replicas(ms: float, keys_per_rank: int, ws: int, device=None):
+    """Whole-job throughput of ws independent replicas (no collective touches
+    the data): the step time is the maximum over ranks, value = the keys all
+    ranks sorted / that time (Gkeys/s).  Returns (ms, value)."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, keys_per_rank * ws / (ms / 1e3) / 1e9
+
+
 def run_ours(args, ws, rank, local):
     import torch
     import paper_2402_01816_gb300 as g
@@ -470,18 +483,11 @@ def run_ours(args, ws, rank, local):
         raise RuntimeError(f"device status {status} during the timed region")
     clocks = clk.summary()
 
-    ms = statistics.mean(step_ms)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    keys_per_step = n * len(combos) * ws
-    value = keys_per_step / (ms / 1e3) / 1e9
+    ms, value = aggregate_replicas(statistics.mean(step_ms), n * len(combos), ws, dev)
 
-    # Roofline of the dominant kernel: the 100% tier merge pass, over the sorts
-    # that run merge levels (the strictly descending pattern is reversed once and
-    # its merge launches return at once, so they are left out of the average).
+    # Roofline of the dominant merge-level kernel, over the sorts that run merge
+    # levels (the strictly descending pattern is reversed once and its merge
+    # launches return at once, so they are left out of the average).
     peak, peak_kind = load_peaks()
     moving = [c for c in combos if c[0] != "desc"]
     total_kernel_ms = sum(t for _, _, t in prof)
