@@ -195,8 +195,30 @@ static __global__ void reverse_kernel(uint64_t* keys, uint32_t* vals, int64_t n,
 {
     if (presorted[0] != 0 || presorted[1] == 0) return;
     const int64_t half = n / 2;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < half;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (n % 8 == 0 && ((uintptr_t)keys & 15) == 0 && ((uintptr_t)vals & 15) == 0) {
+        // groups of four: group g = elements [4g, 4g + 4) and its mirror
+        // [n - 4 - 4g, n - 4g), both 16-byte aligned, swapped with 16-byte accesses
+        for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < half / 4; g += stride) {
+            const int64_t i0 = 4 * g, j0 = n - 4 - 4 * g;
+            ulonglong2* fk = reinterpret_cast<ulonglong2*>(keys + i0);
+            ulonglong2* bk = reinterpret_cast<ulonglong2*>(keys + j0);
+            const ulonglong2 a01 = fk[0], a23 = fk[1], b01 = bk[0], b23 = bk[1];
+            fk[0] = make_ulonglong2(b23.y, b23.x);
+            fk[1] = make_ulonglong2(b01.y, b01.x);
+            bk[0] = make_ulonglong2(a23.y, a23.x);
+            bk[1] = make_ulonglong2(a01.y, a01.x);
+            if (vals) {
+                uint4* fv = reinterpret_cast<uint4*>(vals + i0);
+                uint4* bv = reinterpret_cast<uint4*>(vals + j0);
+                const uint4 x = *fv, y = *bv;
+                *fv = make_uint4(y.w, y.z, y.y, y.x);
+                *bv = make_uint4(x.w, x.z, x.y, x.x);
+            }
+        }
+        return;
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < half; i += stride) {
         int64_t j = n - 1 - i;
         uint64_t a = keys[i], b = keys[j];
         keys[i] = b; keys[j] = a;

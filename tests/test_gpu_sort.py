@@ -165,3 +165,14 @@ def test_frogsort2_workspace_is_p_of_data():
     for p in (0.25, 0.1):
         ws = g.gns_workspace_bytes(n, p)
         assert 12 * p * n <= ws < 12 * p * n + 0.1 * n     # %RAM = 1 + p + under 1%
+
+
+@pytest.mark.parametrize("bf", TIERS)
+@pytest.mark.parametrize("n", [8, 16, 4 * TILE, 4 * TILE + 4, 8 * TILE + 2, 1 << 20])
+def test_strictly_descending_sizes(n, bf):
+    """Strictly descending input is reversed once (Octosort): the 16-byte
+    group path (n a multiple of 8) and the element path."""
+    need_gpu()
+    keys = np.arange(n, 0, -1, dtype=np.float64) * 0.5
+    _run(keys, 0, bf)
+    _run(keys, 0, bf, with_payload=False)
