@@ -234,6 +234,13 @@ def learned_vs_plain(dev, n=1 << 28):
     t_learned = _time_ms(lambda: g.gns_learned_sort(kt, pt), restore)
     t_first = _time_ms(lambda: g.gns_learned_sort(kt, pt, train_steps=0), restore)
     t_plain = _time_ms(lambda: g.gns_sort(kt, pt), restore)
+    # the same at the 50% tier: the half-buffer learned form against Frogsort1
+    restore()
+    rep_half = g.gns_learned_sort(kt, pt, buffer_fraction=0.5, report=True)
+    t_learned_half = _time_ms(lambda: g.gns_learned_sort(kt, pt, buffer_fraction=0.5), restore)
+    t_plain_half = _time_ms(lambda: g.gns_sort(kt, pt, buffer_fraction=0.5), restore)
+    ram_half = 1.0 + g.gns_workspace_bytes(n, 0.5, 1) / (12.0 * n)
+    ram_plain_half = 1.0 + g.gns_workspace_bytes(n, 0.5, 0) / (12.0 * n)
     if g.gns_stream_status() != 0:
         raise RuntimeError("device status error in learned_vs_plain")
     del keys, pay, kt, pt
@@ -243,7 +250,13 @@ def learned_vs_plain(dev, n=1 << 28):
             "learned_ms": t_learned, "plain_ms": t_plain, "first_stage_only_ms": t_first,
             "learned_gkeys_s": n / t_learned / 1e6, "plain_gkeys_s": n / t_plain / 1e6,
             "speedup_vs_plain": t_plain / t_learned, "speedup_vs_first_stage_only": t_first / t_learned,
-            "report": rep}
+            "report": rep,
+            "at_50pct": {"learned_ms": t_learned_half, "plain_ms": t_plain_half,
+                         "speedup_vs_plain": t_plain_half / t_learned_half,
+                         "pct_ram_learned": ram_half, "pct_ram_plain": ram_plain_half,
+                         "t_footprint_learned_ms": ram_half * t_learned_half,
+                         "t_footprint_plain_ms": ram_plain_half * t_plain_half,
+                         "report": rep_half}}
 
 
 def batched_vs_plain(dev, nseg=65536, per_segment_sample=2048):
@@ -296,14 +309,13 @@ def batched_vs_plain(dev, nseg=65536, per_segment_sample=2048):
 # ------------------------------------------------------------------ our arm
 def large_low_memory(dev, n=1 << 31):
     """2^31 float64 keys + uint32 index payload at the 50% tier (and the 100%
-    tier beside it): time, %RAM and tFootprint per pattern.  The learned path
-    has no 50% form, so its call at buffer_fraction 0.5 is the plain 50% sort."""
+    tier beside it), plain and learned-splitter: time, %RAM and tFootprint per
+    pattern."""
     import torch
     import paper_2402_01816_gb300 as g
     from paper_2402_01816_gb300 import inputs
     out = {"workload": "large low-memory run: 2^31 float64 keys + uint32 index payload (24 GiB), "
-                       "patterns permut and presorted_runs (blocks of 2^16, every 10th sorted)",
-           "learned_at_50pct": "falls back to the plain 50% sort (no learned 50% form)"}
+                       "patterns permut and presorted_runs (blocks of 2^16, every 10th sorted)"}
     pay = torch.arange(n, dtype=torch.int64, device=dev).to(torch.int32)
     for pattern in ("permut", "presorted_runs"):
         keys = inputs.make_keys_device(pattern, n, seed=0, device=dev)
@@ -319,6 +331,13 @@ def large_low_memory(dev, n=1 << 31):
             ram = 1.0 + g.gns_workspace_bytes(n, bf) / (12.0 * n)
             out[f"{pattern}@{int(bf * 100)}%"] = {"ms": t, "gkeys_s": n / t / 1e6, "pct_ram": ram,
                                                  "t_footprint_ms": ram * t}
+        restore()
+        rep = g.gns_learned_sort(kt, pt, buffer_fraction=0.5, report=True)
+        t = _time_ms(lambda: g.gns_learned_sort(kt, pt, buffer_fraction=0.5), restore, reps=2)
+        ram = 1.0 + g.gns_workspace_bytes(n, 0.5, 1) / (12.0 * n)
+        out[f"{pattern}@50%-learned"] = {"ms": t, "gkeys_s": n / t / 1e6, "pct_ram": ram,
+                                         "t_footprint_ms": ram * t, "fallback": rep["fallback"],
+                                         "max_bucket": rep["max_bucket"]}
         if g.gns_stream_status() != 0:
             raise RuntimeError("device status error in large_low_memory")
         del keys, kt, pt

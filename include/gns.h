@@ -222,11 +222,24 @@ void gns_segmented_release(gns_stream_t stream);
  *      "DIET-method" section: an all-tied part needs no sorting); a bucket
  *      that came out larger than `overfull_factor` times the mean is simply
  *      sorted by more merge levels of the same merge path (the plain merge
- *      path is the fallback for it), and if the splitters were not
- *      non-decreasing, or buffer_fraction < 1, or n < 2^20, the whole call
- *      falls back to gns_sort.
+ *      path is the fallback for it).
+ * buffer_fraction:
+ *   >= 1.0      the three phases on the whole array; scratch ~ 16 n bytes for
+ *               the partition, then ~ 12 n for the bucket sort (n >= 2^20).
+ *   [0.5, 1.0)  half-buffer form (n >= 2^22): the array is the four leaves of
+ *               a two-level Frogsort1 tree ("Frogsort1" section: floor(n/2)
+ *               buffer slots after the data, here floor(n/2) + 1024).  Leaves
+ *               are learned-sorted right to left, each in place with its
+ *               scratch carved out of the slots free at that moment, moved to
+ *               its gapped data slots, and the tree's two in-place symmetric
+ *               merge levels ("Symmetric merging" section) finish the sort.
+ *               Scratch ~ 6 n bytes + a few MiB (%RAM about 1.5).
+ *   otherwise   (fewer keys, buffer_fraction < 0.5, or no room in the plan)
+ *               the whole call is gns_sort at this buffer_fraction, and the
+ *               report says fallback = 1.
  * params: NULL = defaults.  report: if not NULL, the call synchronises the
- * stream and fills it.
+ * stream and fills it (half-buffer form: phase times and bucket counts summed
+ * over the four leaves, max_bucket and final_loss their maxima).
  */
 typedef struct {
     int train_steps;         /* Adam steps (default 64); 0 = no network:
@@ -269,6 +282,11 @@ int gns_mlp_loss_grad(const float* params, const float* x, const float* t, int64
                       float* loss, gns_stream_t stream);
 int gns_mlp_train(const float* x, const float* t, int64_t m, const float* params_in, float* params_out,
                   float* loss_out, int steps, int batch, float learning_rate, gns_stream_t stream);
+
+/* Test hook: 1 if gns_learned_sort at a buffer_fraction in [0.5, 1) takes its
+ * half-buffer form for n keys, with and without a payload (the host-side
+ * memory plan fits), else 0.  Runs on the host only. */
+int gns_learned_half_plan_ok(int64_t n);
 
 /* The initial network of the learned sort (1153 floats, host memory). */
 void gns_mlp_init_params(float* params_host);

@@ -69,6 +69,7 @@ def lib() -> ctypes.CDLL:
                 "gns_kernel_name": ([i32], ctypes.c_char_p),
                 "gns_set_wait_limit_ns": ([u64], None),
                 "gns_debug_skip_publish": ([i64], None),
+                "gns_learned_half_plan_ok": ([i64], i32),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -189,6 +190,12 @@ def gns_learned_sort(keys, payload=None, order: int = ASCENDING, buffer_fraction
     if rep is None:
         return None
     return {name: getattr(rep, name) for name, _ in LearnedReport._fields_}
+
+
+def gns_learned_half_plan_ok(n: int) -> bool:
+    """True if gns_learned_sort at a buffer fraction in [0.5, 1) runs its
+    half-buffer form for n keys (host-side plan only; needs no GPU)."""
+    return bool(lib().gns_learned_half_plan_ok(int(n)))
 
 
 def gns_mlp_init_params():

@@ -196,7 +196,7 @@ const char* kernel_names[K_COUNT] = {
     "run_detect", "reverse", "tile_sort", "merge_partition", "merge_pass", "frog_plan", "frog_setup",
     "frog_partition", "frog_merge", "err_publish", "seg_plan", "seg_tile", "seg_merge", "learn_sample",
     "learn_fit", "learn_split", "learn_hist", "learn_scan", "learn_scatter", "learn_verify", "mlp_forward",
-    "mlp_backward", "mlp_adam", "noalloc_sort"};
+    "mlp_backward", "mlp_adam", "noalloc_sort", "learn_half_move"};
 
 }  // namespace gns
 
@@ -285,10 +285,7 @@ size_t gns_workspace_bytes(int64_t n, double buffer_fraction, int kind)
 {
     if (n < 0 || isnan(buffer_fraction)) return 0;
     if (kind == GNS_WS_SORT) return sort_workspace_bytes(n, buffer_fraction);
-    if (kind == GNS_WS_LEARNED) {
-        if (buffer_fraction < 1.0 || n < (1ll << 20)) return sort_workspace_bytes(n, buffer_fraction);
-        return learned_workspace_bytes(n);
-    }
+    if (kind == GNS_WS_LEARNED) return learned_workspace_bytes(n, buffer_fraction);
     return 0;
 }
 

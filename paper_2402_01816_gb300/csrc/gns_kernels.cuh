@@ -314,7 +314,7 @@ struct FrogNode {
     int32_t side, pad;
 };
 
-__device__ __forceinline__ void frog_split(const FrogNode& p, FrogNode& L, FrogNode& R)
+__host__ __device__ __forceinline__ void frog_split(const FrogNode& p, FrogNode& L, FrogNode& R)
 {
     int64_t n_outer = (p.n + 1) / 2, n_inner = p.n - n_outer;
     int64_t b_outer = n_outer / 2, b_inner = p.b - b_outer;
@@ -325,7 +325,7 @@ __device__ __forceinline__ void frog_split(const FrogNode& p, FrogNode& L, FrogN
     L.s = p.s; R.s = p.s + L.n;
 }
 
-__device__ __forceinline__ int64_t frog_data_slot(const FrogNode& x) { return x.side == 0 ? x.r : x.r + x.b; }
+__host__ __device__ __forceinline__ int64_t frog_data_slot(const FrogNode& x) { return x.side == 0 ? x.r : x.r + x.b; }
 
 struct Slots {
     uint64_t* k0; uint32_t* v0;   // caller arrays: slots [0, n)

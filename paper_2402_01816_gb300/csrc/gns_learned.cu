@@ -11,7 +11,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "gns_internal.h"
 #include "gns_kernels.cuh"
@@ -922,32 +925,41 @@ LearnLayout learn_layout(int64_t n, bool with_vals)
     return o;
 }
 
+// Scratch of the partition and the bucket sort when the caller provides it
+// (the half-buffer form): a key and a payload buffer of n elements each (the
+// partition's scatter buffer, later the bucket sort's ping-pong buffer), the
+// two bucket-id arrays and the per-tile digit counts.
+struct LearnScratch {
+    uint64_t* bufk;
+    uint32_t* bufv;
+    uint16_t* bidA;
+    uint16_t* bidB;
+    uint32_t* counts;   // 64 x ceil(n / PART_TILE)
+};
+
 }  // namespace
 
-size_t learned_workspace_bytes(int64_t n)
-{
-    const LearnLayout l = learn_layout(n, true);
-    const size_t bucket_sort = segmented_workspace_bytes(n, NBUCKETS);
-    return l.total + (l.big > bucket_sort ? l.big : bucket_sort);   // peak: the two phases do not overlap
-}
-
-// The learned sort on the device (all checks done by the caller).
+// The learned sort on the device (all checks done by the caller).  xs: scratch
+// provided by the caller (nullptr: allocated here).
 int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, const gns_learned_params& prm,
-                        gns_learned_report* rep, cudaStream_t s)
+                        gns_learned_report* rep, cudaStream_t s, const LearnScratch* xs = nullptr)
 {
     learn_init_attributes();
     const LearnLayout lay = learn_layout(n, vals != nullptr);
     char* ws = (char*)ws_alloc(lay.total, s);
     if (!ws) return GNS_ERR_OOM;
-    char* big = (char*)ws_alloc(lay.big, s);
-    if (!big) {
-        ws_free(ws, s);
-        return GNS_ERR_OOM;
+    char* big = nullptr;
+    if (!xs) {
+        big = (char*)ws_alloc(lay.big, s);
+        if (!big) {
+            ws_free(ws, s);
+            return GNS_ERR_OOM;
+        }
     }
     int rc = GNS_OK;
-    uint64_t* bufk = (uint64_t*)(big + lay.bufk);
-    uint32_t* bufv = vals ? (uint32_t*)(big + lay.bufv) : nullptr;
-    uint32_t* counts = (uint32_t*)(big + lay.counts);
+    uint64_t* bufk = xs ? xs->bufk : (uint64_t*)(big + lay.bufk);
+    uint32_t* bufv = vals ? (xs ? xs->bufv : (uint32_t*)(big + lay.bufv)) : nullptr;
+    uint32_t* counts = xs ? xs->counts : (uint32_t*)(big + lay.counts);
     uint64_t* sample = (uint64_t*)(ws + lay.sample);
     float* x = (float*)(ws + lay.x);
     float* t = (float*)(ws + lay.t);
@@ -960,8 +972,8 @@ int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, con
     LearnMeta* meta = (LearnMeta*)(ws + lay.meta);
     unsigned long long* rowtot = (unsigned long long*)(ws + lay.rowtot);
     unsigned long long* btot = (unsigned long long*)(ws + lay.btot);
-    uint16_t* bidA = (uint16_t*)(big + lay.bidA);
-    uint16_t* bidB = (uint16_t*)(big + lay.bidB);
+    uint16_t* bidA = xs ? xs->bidA : (uint16_t*)(big + lay.bidA);
+    uint16_t* bidB = xs ? xs->bidB : (uint16_t*)(big + lay.bidB);
     uint8_t* tied = (uint8_t*)(ws + lay.tied);
     int* diff = (int*)(ws + lay.diff);
     int64_t* boff = (int64_t*)(ws + lay.off);
@@ -1038,10 +1050,11 @@ int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, con
     LTRY(launch(K_LEARN_VERIFY, tied_final_kernel, dim3(NBUCKETS / 256), dim3(256), 0, s, (const int64_t*)boff,
                 (const uint64_t*)spl, (const int*)diff, tied, meta));
     if (rep) LTRY(cudaEventRecord(ev[2], s));
-    ws_free(big, s);
+    if (big) ws_free(big, s);
     big = nullptr;
     // 3. every bucket is a segment
-    rc = segmented_sort_direct(keys, vals, boff, NBUCKETS, n, mode, (const uint8_t*)tied, s);
+    rc = segmented_sort_direct(keys, vals, boff, NBUCKETS, n, mode, (const uint8_t*)tied, s, xs ? xs->bufk : nullptr,
+                               xs ? xs->bufv : nullptr);
     if (rc != GNS_OK) goto done;
     if (rep) {
         LTRY(cudaEventRecord(ev[3], s));
@@ -1070,11 +1083,260 @@ done:
     return rc;
 }
 
+// ---------------------------------------------------------- the <= 50% form
+// Merge levels D-1 .. 0 of a balanced Frogsort1 tree (gns_sort.cu) whose
+// leaves already hold sorted, order-mapped data at their data slots: nodes in
+// heap order on the device; ctl[0..1] must be 0 and ctl[2] is the call's error
+// word; ws holds frog_levels_bytes(n, D) bytes.
+size_t frog_levels_bytes(int64_t n, int D);
+int frog_levels_device(const Slots& sl, const FrogNode* nodes, int D, int mode, int* ctl, char* ws, cudaStream_t s);
+
+namespace {
+
+// Under a buffer of about half the data ("Frogsort1" section: floor(n/2)
+// buffer slots appended to the data), the learned sort runs on the four leaves
+// of a two-level Frogsort1 tree, and the tree's two in-place merge levels
+// ("Symmetric merging": inner end to outer end) finish the sort:
+//   1. leaves right to left: a leaf's contiguous input range is sorted in
+//      place by the learned sort, whose scatter buffer, bucket ids, digit
+//      counts and bucket-sort buffer are carved out of the slots free at that
+//      moment (the buffer, input ranges of leaves already moved);
+//   2. the sorted leaf moves to its data slots of the gapped layout, its keys
+//      order-mapped on the way (the merge levels compare mapped keys).  A
+//      destination never lies left of its source, so moving leaves right to
+//      left overwrites only inputs that are already consumed;
+//   3. the merge levels of depths 1 and 0.
+// The root holds HALF_EXTRA buffer slots more than floor(n/2): when the left
+// half is odd, its left leaf is one element longer than the free ranges
+// around it, and the extra slots give it a contiguous scratch range.
+constexpr int64_t HALF_EXTRA = 1024;
+constexpr int64_t HALF_MIN_N = 1ll << 22;   // leaves of at least 2^20 keys
+
+struct HalfRegion {
+    int arr;       // 0: keys [0, n), 1: payload [0, n), 2: buffer keys, 3: buffer payload
+    int64_t off;   // byte offset in that array; the region starts at the next 256-byte boundary
+};
+struct HalfLeaf {
+    int64_t m, src, dst;   // elements, first input index, first data slot
+    HalfRegion bufk, bufv, bidA, bidB, counts;
+};
+struct HalfPlan {
+    int64_t n, b;
+    FrogNode nodes[7];     // heap order: root, L, R, LL, LR, RL, RR
+    HalfLeaf leaf[4];      // in input order: LL, LR, RL, RR
+};
+struct HalfNodes {
+    FrogNode x[7];
+};
+
+// The tree and, for every leaf, where its scratch goes; false if a leaf's
+// scratch does not fit into the slots free while it is sorted (then the caller
+// runs the plain sort).  Without a payload there are no payload arrays to
+// carve from, and no payload buffer to place.
+bool half_plan(int64_t n, bool with_vals, HalfPlan& P)
+{
+    P.n = n;
+    P.b = n / 2 + HALF_EXTRA;
+    FrogNode root;
+    root.n = n; root.b = P.b; root.r = 0; root.s = 0; root.side = 0; root.pad = 0;
+    P.nodes[0] = root;
+    frog_split(P.nodes[0], P.nodes[1], P.nodes[2]);
+    frog_split(P.nodes[1], P.nodes[3], P.nodes[4]);
+    frog_split(P.nodes[2], P.nodes[5], P.nodes[6]);
+    const int64_t total = n + P.b;
+    for (int i = 0; i < 4; ++i) {
+        const FrogNode& x = P.nodes[3 + i];
+        P.leaf[i] = HalfLeaf{};
+        P.leaf[i].m = x.n;
+        P.leaf[i].src = x.s;
+        P.leaf[i].dst = frog_data_slot(x);
+    }
+    auto overlap = [](int64_t a0, int64_t a1, int64_t b0, int64_t b1) { return a0 < b1 && b0 < a1; };
+    struct Free {
+        int arr;
+        int64_t off, len;
+    };
+    for (int j = 3; j >= 0; --j) {
+        HalfLeaf& L = P.leaf[j];
+        if (L.m <= 0 || L.dst < L.src || L.dst + L.m > total) return false;
+        if (L.dst != L.src && overlap(L.src, L.src + L.m, L.dst, L.dst + L.m)) return false;
+        // slots in use while leaf j is sorted: inputs of leaves 0..j, data of leaves j+1..3
+        std::vector<std::pair<int64_t, int64_t>> busy;
+        for (int i = 0; i <= j; ++i) busy.push_back({P.leaf[i].src, P.leaf[i].src + P.leaf[i].m});
+        for (int i = j + 1; i < 4; ++i) busy.push_back({P.leaf[i].dst, P.leaf[i].dst + P.leaf[i].m});
+        for (int q = 0; q < (int)busy.size(); ++q)
+            if (q != j && overlap(busy[q].first, busy[q].second, L.dst, L.dst + L.m)) return false;
+        std::sort(busy.begin(), busy.end());
+        std::vector<Free> fr;
+        auto push_free = [&](int64_t a, int64_t c) {   // free slots [a, c): a key and a payload region per array
+            if (a < n) {
+                const int64_t e = c < n ? c : n;
+                fr.push_back({0, 8 * a, 8 * (e - a)});
+                if (with_vals) fr.push_back({1, 4 * a, 4 * (e - a)});
+                a = e;
+            }
+            if (a < c) {
+                fr.push_back({2, 8 * (a - n), 8 * (c - a)});
+                if (with_vals) fr.push_back({3, 4 * (a - n), 4 * (c - a)});
+            }
+        };
+        int64_t cur = 0;
+        for (const auto& iv : busy) {
+            if (iv.first > cur) push_free(cur, iv.first);
+            if (iv.second > cur) cur = iv.second;
+        }
+        if (cur < total) push_free(cur, total);
+        // best fit, largest request first; 256 bytes of slack for the alignment
+        const int64_t req[5] = {8 * L.m, 4 * L.m, 2 * L.m, 2 * L.m, 256 * cdiv(L.m, PART_TILE)};
+        HalfRegion* to[5] = {&L.bufk, &L.bufv, &L.bidA, &L.bidB, &L.counts};
+        for (int r = 0; r < 5; ++r) {
+            if (r == 1 && !with_vals) continue;
+            const int64_t need = req[r] + 256;
+            int best = -1;
+            for (int q = 0; q < (int)fr.size(); ++q)
+                if (fr[q].len >= need && (best < 0 || fr[q].len < fr[best].len)) best = q;
+            if (best < 0) return false;
+            to[r]->arr = fr[best].arr;
+            to[r]->off = fr[best].off;
+            fr[best].off += need;
+            fr[best].len -= need;
+        }
+    }
+    return true;
+}
+
+size_t half_main_bytes(const HalfPlan& P, bool with_vals, size_t* o_bufv, size_t* o_nodes, size_t* o_levels)
+{
+    size_t off = 256;                       // control words
+    off += align256((size_t)P.b * 8);       // buffer keys
+    *o_bufv = off;
+    off += with_vals ? align256((size_t)P.b * 4) : 0;
+    *o_nodes = off;
+    off += align256(sizeof(HalfNodes));
+    *o_levels = off;
+    return off + frog_levels_bytes(P.n, 2);
+}
+
+__global__ void half_nodes_kernel(HalfNodes t, FrogNode* out)
+{
+    if (threadIdx.x < 7) out[threadIdx.x] = t.x[threadIdx.x];
+}
+
+// A sorted leaf at input indices [src, src + m) moves to data slots
+// [dst, dst + m), its keys order-mapped (dst == src: in place).
+__global__ void __launch_bounds__(256) half_move_kernel(Slots sl, int64_t src, int64_t dst, int64_t m, int mode)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        const uint64_t k = encode_key(sl.k0[src + i], mode);
+        if (sl.v0) {
+            const uint32_t v = sl.v0[src + i];
+            *sl.vp(dst + i) = v;
+        }
+        *sl.kp(dst + i) = k;
+    }
+}
+
+}  // namespace
+
+// The learned sort within about half a buffer (all checks done by the caller).
+// GNS_ERR_UNSUPPORTED (nothing launched): the memory plan does not fit.
+int learned_half_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, const gns_learned_params& prm,
+                             gns_learned_report* rep, cudaStream_t s)
+{
+    HalfPlan P;
+    if (!half_plan(n, vals != nullptr, P)) return GNS_ERR_UNSUPPORTED;
+    size_t o_bufv = 0, o_nodes = 0, o_levels = 0;
+    const size_t total = half_main_bytes(P, vals != nullptr, &o_bufv, &o_nodes, &o_levels);
+    char* ws = (char*)ws_alloc(total, s);
+    if (!ws) return GNS_ERR_OOM;
+    int rc = GNS_OK;
+    int* ctl = (int*)ws;
+    Slots sl;
+    sl.k0 = keys; sl.v0 = vals; sl.n = n; sl.b = P.b;
+    sl.k1 = (uint64_t*)(ws + 256);
+    sl.v1 = vals ? (uint32_t*)(ws + o_bufv) : nullptr;
+    FrogNode* nodes = (FrogNode*)(ws + o_nodes);
+    const uintptr_t base[4] = {(uintptr_t)sl.k0, (uintptr_t)sl.v0, (uintptr_t)sl.k1, (uintptr_t)sl.v1};
+    auto at = [&](const HalfRegion& r) -> void* { return (void*)((base[r.arr] + (uintptr_t)r.off + 255) & ~(uintptr_t)255); };
+    HalfNodes hn;
+    for (int i = 0; i < 7; ++i) hn.x[i] = P.nodes[i];
+    if (rep) memset(rep, 0, sizeof(*rep));
+#define HTRY(x)                     \
+    do {                            \
+        if ((x) != cudaSuccess) {   \
+            rc = GNS_ERR_CUDA;      \
+            goto done;              \
+        }                           \
+    } while (0)
+    HTRY(cudaMemsetAsync(ctl, 0, 256, s));
+    for (int j = 3; j >= 0; --j) {
+        const HalfLeaf& L = P.leaf[j];
+        LearnScratch xs;
+        xs.bufk = (uint64_t*)at(L.bufk);
+        xs.bufv = vals ? (uint32_t*)at(L.bufv) : nullptr;
+        xs.bidA = (uint16_t*)at(L.bidA);
+        xs.bidB = (uint16_t*)at(L.bidB);
+        xs.counts = (uint32_t*)at(L.counts);
+        gns_learned_report lr;
+        rc = learned_sort_device(keys + L.src, vals ? vals + L.src : nullptr, L.m, mode, prm, rep ? &lr : nullptr, s,
+                                 &xs);
+        if (rc != GNS_OK) goto done;
+        if (rep) {
+            rep->nonempty_buckets += lr.nonempty_buckets;
+            rep->max_bucket = lr.max_bucket > rep->max_bucket ? lr.max_bucket : rep->max_bucket;
+            rep->overfull_buckets += lr.overfull_buckets;
+            rep->tied_buckets += lr.tied_buckets;
+            rep->final_loss = lr.final_loss > rep->final_loss ? lr.final_loss : rep->final_loss;
+            rep->fit_ms += lr.fit_ms;
+            rep->partition_ms += lr.partition_ms;
+            rep->bucket_sort_ms += lr.bucket_sort_ms;
+        }
+        HTRY(launch(K_LEARN_HALF, half_move_kernel, dim3((unsigned)imin_h(cdiv(L.m, 256), (int64_t)sms_now() * 8)),
+                    dim3(256), 0, s, sl, L.src, L.dst, L.m, mode));
+    }
+    HTRY(launch(K_LEARN_HALF, half_nodes_kernel, dim3(1), dim3(32), 0, s, hn, nodes));
+    rc = frog_levels_device(sl, (const FrogNode*)nodes, 2, mode, ctl, ws + o_levels, s);
+#undef HTRY
+done:
+    ws_free(ws, s);
+    return rc;
+}
+
+size_t learned_workspace_bytes(int64_t n, double bf)
+{
+    if (n >= (1ll << 20) && bf >= 1.0) {
+        const LearnLayout l = learn_layout(n, true);
+        const size_t bucket_sort = segmented_workspace_bytes(n, NBUCKETS);
+        return l.total + (l.big > bucket_sort ? l.big : bucket_sort);   // peak: the two phases do not overlap
+    }
+    HalfPlan P;
+    if (n >= HALF_MIN_N && bf >= 0.5 && half_plan(n, true, P)) {
+        size_t o_bufv = 0, o_nodes = 0, o_levels = 0;
+        size_t leaf = 0;
+        for (int i = 0; i < 4; ++i) {
+            const int64_t m = P.leaf[i].m;
+            const size_t x = learn_layout(m, true).total + segmented_workspace_bytes(m, NBUCKETS, true) +
+                             sort_workspace_bytes(SAMPLE_M, 1.0);
+            leaf = x > leaf ? x : leaf;
+        }
+        return half_main_bytes(P, true, &o_bufv, &o_nodes, &o_levels) + leaf;
+    }
+    return sort_workspace_bytes(n, bf);
+}
+
 }  // namespace gns
 
 using namespace gns;
 
 extern "C" {
+
+int gns_learned_half_plan_ok(int64_t n)
+{
+    HalfPlan P, Q;
+    return (n >= HALF_MIN_N && half_plan(n, true, P) && half_plan(n, false, Q)) ? 1 : 0;
+}
+
 
 void gns_mlp_init_params(float* params_host)
 {
@@ -1129,15 +1391,23 @@ int gns_learned_sort(double* keys, uint32_t* payload, int64_t n, int order, doub
     if (((uintptr_t)keys & 7) || ((uintptr_t)payload & 3)) return GNS_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     if (report) memset(report, 0, sizeof(*report));
-    if (buffer_fraction < 1.0 || n < (1ll << 20)) {
-        // the partition needs a full buffer and enough keys to pay for the fit
-        if (report) report->fallback = 1;
-        int rc = gns_sort(keys, payload, n, order, buffer_fraction, stream);
+    const int mode = order == GNS_DESCENDING ? MODE_DESC : 0;
+    int rc = GNS_ERR_UNSUPPORTED;
+    if (buffer_fraction >= 1.0 && n >= (1ll << 20))
+        rc = learned_sort_device((uint64_t*)keys, payload, n, mode, prm, report, s);
+    else if (buffer_fraction >= 0.5 && n >= HALF_MIN_N)
+        rc = learned_half_sort_device((uint64_t*)keys, payload, n, mode, prm, report, s);
+    if (rc == GNS_ERR_UNSUPPORTED) {
+        // too few keys to pay for the fit, a buffer below one half, or no room
+        // for a leaf's scratch: the plain sort at this buffer fraction
+        if (report) {
+            memset(report, 0, sizeof(*report));
+            report->fallback = 1;
+        }
+        rc = gns_sort(keys, payload, n, order, buffer_fraction, stream);
         if (rc == GNS_OK && report) rc = gns_stream_status(stream);
         return rc;
     }
-    const int mode = order == GNS_DESCENDING ? MODE_DESC : 0;
-    int rc = learned_sort_device((uint64_t*)keys, payload, n, mode, prm, report, s);
     return finish_call(rc, s);
 }
 

@@ -295,15 +295,17 @@ struct SegLayout {
     int64_t max_items;
 };
 
-SegLayout seg_layout(int64_t n, int64_t nseg, bool with_vals)
+// ext_buf: the caller provides the n-element ping-pong buffer, which is then
+// not part of the workspace.
+SegLayout seg_layout(int64_t n, int64_t nseg, bool with_vals, bool ext_buf = false)
 {
     SegLayout o{};
     size_t off = 0;
     o.L = max_levels(n);
     o.max_items = ceil_div(n, CHUNK) + nseg;
     o.ctl = off; off += 256;
-    o.bufk = off; off += align256((size_t)n * 8);
-    o.bufv = off; off += with_vals ? align256((size_t)n * 4) : 0;
+    o.bufk = off; off += ext_buf ? 0 : align256((size_t)n * 8);
+    o.bufv = off; off += (with_vals && !ext_buf) ? align256((size_t)n * 4) : 0;
     o.rows = off; off += align256((size_t)(2 + o.L) * (size_t)(nseg + 1) * 8);
     o.levels = off; off += align256((size_t)nseg);
     o.list = off; off += align256((size_t)o.max_items * sizeof(SegChunk));
@@ -331,12 +333,12 @@ void seg_init_attributes()
 // Enqueues the whole segmented sort on s (keys/vals in place, ws laid out by lay).
 cudaError_t seg_enqueue(uint64_t* keys, uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, int mode,
                         const SegSchedule& sch, char* ws, const SegLayout& lay, cudaStream_t s,
-                        const uint8_t* skip = nullptr)
+                        const uint8_t* skip = nullptr, uint64_t* xbufk = nullptr, uint32_t* xbufv = nullptr)
 {
     int* ctl = (int*)(ws + lay.ctl);
     int* call_err = ctl + 2;
-    uint64_t* bufk = (uint64_t*)(ws + lay.bufk);
-    uint32_t* bufv = vals ? (uint32_t*)(ws + lay.bufv) : nullptr;
+    uint64_t* bufk = xbufk ? xbufk : (uint64_t*)(ws + lay.bufk);
+    uint32_t* bufv = vals ? (xbufk ? xbufv : (uint32_t*)(ws + lay.bufv)) : nullptr;
     int64_t* rows = (int64_t*)(ws + lay.rows);
     uint8_t* levels = (uint8_t*)(ws + lay.levels);
     SegChunk* list = (SegChunk*)(ws + lay.list);
@@ -551,19 +553,25 @@ int segmented_sort_device(uint64_t* keys, uint32_t* vals, const int64_t* off, in
     return cudaGraphLaunch(exec, s) == cudaSuccess ? GNS_OK : GNS_ERR_CUDA;
 }
 
-size_t segmented_workspace_bytes(int64_t n, int64_t nseg) { return seg_layout(n, nseg, true).total; }
+size_t segmented_workspace_bytes(int64_t n, int64_t nseg, bool ext_buf)
+{
+    return seg_layout(n, nseg, true, ext_buf).total;
+}
 
 // Segmented sort without tuning or graph capture (schedule 0), for callers that
 // build the segments themselves on the device (the learned-splitter sort).
+// xbufk / xbufv (optional): a caller-provided n-element ping-pong buffer.
 int segmented_sort_direct(uint64_t* keys, uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, int mode,
-                          const uint8_t* skip, cudaStream_t s)
+                          const uint8_t* skip, cudaStream_t s, uint64_t* xbufk, uint32_t* xbufv)
 {
     if (nseg == 0 || n <= 1) return GNS_OK;
     seg_init_attributes();
-    const SegLayout lay = seg_layout(n, nseg, vals != nullptr);
+    const bool ext = xbufk != nullptr && (vals == nullptr || xbufv != nullptr);
+    const SegLayout lay = seg_layout(n, nseg, vals != nullptr, ext);
     char* ws = (char*)ws_alloc(lay.total, s);
     if (!ws) return GNS_ERR_OOM;
-    cudaError_t e = seg_enqueue(keys, vals, off, nseg, n, mode, kDirect, ws, lay, s, skip);
+    cudaError_t e = seg_enqueue(keys, vals, off, nseg, n, mode, kDirect, ws, lay, s, skip, ext ? xbufk : nullptr,
+                                ext ? xbufv : nullptr);
     ws_free(ws, s);
     return e == cudaSuccess ? GNS_OK : GNS_ERR_CUDA;
 }

@@ -525,4 +525,51 @@ done:
     return rc;
 }
 
+size_t frog_levels_bytes(int64_t n, int D)
+{
+    int64_t max_split = 1;
+    for (int d = 0; d < D; ++d) {
+        const int64_t e = (1ll << d) * frog_chunks(n, d);
+        if (e > max_split) max_split = e;
+    }
+    return align256((size_t)max_split * 8) + align256((size_t)max_split * sizeof(FrogItem)) +
+           align256((size_t)max_split * 4) + align256((size_t)(D + 1) * 4);
+}
+
+int frog_levels_device(const Slots& sl, const FrogNode* nodes, int D, int mode, int* ctl, char* ws, cudaStream_t s)
+{
+    init_attributes();
+    int rc = GNS_OK;
+    int64_t max_split = 1;
+    for (int d = 0; d < D; ++d) {
+        const int64_t e = (1ll << d) * frog_chunks(sl.n, d);
+        if (e > max_split) max_split = e;
+    }
+    int64_t* splits = (int64_t*)ws;
+    FrogItem* items = (FrogItem*)(ws + align256((size_t)max_split * 8));
+    int* flags = (int*)((char*)items + align256((size_t)max_split * sizeof(FrogItem)));
+    int* tickets = (int*)((char*)flags + align256((size_t)max_split * 4));
+    int* call_err = ctl + 2;
+    const int* skip = ctl;
+    const uint64_t limit = wait_limit_ns();
+    GNS_TRY(cudaMemsetAsync(flags, 0, align256((size_t)max_split * 4) + align256((size_t)(D + 1) * 4), s));
+    for (int d = D - 1; d >= 0; --d) {
+        const int64_t nnodes = 1ll << d;
+        const int64_t nch = frog_chunks(sl.n, d);
+        const FrogNode* level = nodes + (nnodes - 1);
+        const FrogNode* child = nodes + (2 * nnodes - 1);
+        GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel, dim3((unsigned)ceil_div(nnodes * nch, 256)),
+                       dim3(256), 0, s, sl, level, child, nnodes, nch, (const int64_t*)nullptr, nnodes * nch, splits,
+                       skip));
+        GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel, dim3((unsigned)ceil_div(nnodes * nch, 256)), dim3(256), 0,
+                       s, level, child, nnodes, nch, (const int64_t*)nullptr, nnodes * nch, (const int64_t*)splits,
+                       items, call_err, skip));
+        GNS_TRY(launch_frog_level(sl, (const FrogItem*)items, nnodes * nch, mode, (int)(d == 0), tickets + d, flags,
+                                  D - d, call_err, limit, (int64_t)-1, skip, s));
+    }
+    GNS_TRY(publish_call_error(call_err, s));
+done:
+    return rc;
+}
+
 }  // namespace gns

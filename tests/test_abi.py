@@ -116,3 +116,32 @@ def test_segmented_host_argument_checks(L):
     assert L.gns_segmented_sort_ex(FAKE, 1, None, FAKE, 0, 0, 0, None) == 0     # nothing to sort
     assert L.gns_segmented_sort(FAKE, None, FAKE, -2, None) == -1
     assert L.gns_segmented_sort(FAKE, None, FAKE, 0, None) == 0
+
+
+def test_learned_half_plan_fits_every_size(L):
+    """The half-buffer learned sort's host-side memory plan (leaf scratch carved
+    from the slots free at each step) fits for every n from 2^22 on: all small
+    sizes near the threshold (both parities of every subtree), and random and
+    power-of-two sizes up to 2^33."""
+    import random
+    rng = random.Random(5)
+    sizes = list(range(1 << 22, (1 << 22) + 600))
+    sizes += [1 << k for k in range(22, 34)] + [(1 << k) - 1 for k in range(23, 34)]
+    sizes += [rng.randrange(1 << 22, 1 << 33) for _ in range(3000)]
+    for n in sizes:
+        assert L.gns_learned_half_plan_ok(n) == 1, n
+    assert L.gns_learned_half_plan_ok((1 << 22) - 1) == 0       # below the threshold: plain sort
+
+
+@pytest.mark.parametrize("n", [1 << 27, 1 << 31])
+def test_learned_half_buffer_ram(L, n):
+    """%RAM = (12 n + workspace) / 12 n of the half-buffer learned sort: the
+    floor(n/2) + 1024 buffer slots, the merge levels' chunk records (under
+    1/16 byte per key) and a fixed few tens of MiB (network, splitters,
+    key-to-bucket table, plans), i.e. about 1.5."""
+    from paper_2402_01816_gb300 import _native as nat
+    ws = nat.gns_workspace_bytes(n, 0.5, nat.WS_LEARNED)
+    assert 12 * (n // 2) <= ws <= 12 * (n // 2 + 1024) + n // 16 + (32 << 20)
+    assert 1.0 + ws / (12.0 * n) < 1.52
+    # a full buffer: the partition's 16 n bytes dominate
+    assert nat.gns_workspace_bytes(n, 1.0, nat.WS_LEARNED) >= 16 * n

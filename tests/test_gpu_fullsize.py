@@ -69,19 +69,26 @@ def test_small_config_exact():
 N_LARGE = 1 << 31
 
 
+@pytest.mark.parametrize("learned", [False, True])
 @pytest.mark.parametrize("pattern", ["permut", "presorted_runs"])
-def test_large_low_memory_run(pattern):
+def test_large_low_memory_run(pattern, learned):
     """2^31 float64 keys + uint32 index payload at the 50% buffer tier (24 GiB
-    of data, 12 GiB of buffer).  Both patterns are permutations of 1..n, so the
-    sorted keys must be exactly 1..n and the payload must carry every key from
-    its input position; checked on the device."""
+    of data, 12 GiB of buffer), by the plain and by the learned-splitter sort.
+    Both patterns are permutations of 1..n, so the sorted keys must be exactly
+    1..n and the payload must carry every key from its input position; checked
+    on the device."""
     need_gpu()
     import paper_2402_01816_gb300 as g
     kt = inputs.make_keys_device(pattern, N_LARGE, seed=0)
     pt = torch.arange(N_LARGE, dtype=torch.int64, device="cuda").to(torch.int32)
     k_in = kt.clone()
-    assert 1.0 + g.gns_workspace_bytes(N_LARGE, 0.5) / (12.0 * N_LARGE) < 1.52     # %RAM
-    g.gns_sort(kt, pt, buffer_fraction=0.5)
+    kind = 1 if learned else 0
+    assert 1.0 + g.gns_workspace_bytes(N_LARGE, 0.5, kind) / (12.0 * N_LARGE) < 1.52     # %RAM
+    if learned:
+        rep = g.gns_learned_sort(kt, pt, buffer_fraction=0.5, report=True)
+        assert rep["fallback"] == 0
+    else:
+        g.gns_sort(kt, pt, buffer_fraction=0.5)
     assert g.gns_stream_status() == 0
     want = torch.arange(1, N_LARGE + 1, dtype=torch.float64, device="cuda")
     assert torch.equal(kt, want)

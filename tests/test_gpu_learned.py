@@ -9,6 +9,7 @@
   orders, keys only, and its fallbacks;
 * the trained network balances the buckets far better than evenly spaced
   splitters (what the network gains over the method without it);
+* the half-buffer form (buffer_fraction in [0.5, 1)) is bit-exact too;
 * the full learned workload: 2^28 float64 keys from the three-part mixture.
 """
 import numpy as np
@@ -149,6 +150,32 @@ def test_learned_fallbacks():
     assert rep["fallback"] == 1
     rep = _learned(inputs.make_keys("mixture", N, seed=1), train_steps=0)  # no network
     assert rep["fallback"] == 0
+
+
+N_HALF = (1 << 22) + 12347     # four leaves of about 2^20 keys, ragged
+
+
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("pattern", ["mixture", "ties", "permut", "asc_noise", "desc"])
+def test_learned_half_buffer_exact(pattern, order):
+    """The half-buffer form (four learned-sorted leaves of a two-level
+    Frogsort1 tree, then two in-place merge levels) is bit-exact."""
+    need_gpu()
+    rep = _learned(inputs.make_keys(pattern, N_HALF, seed=21), order=order, buffer_fraction=0.5)
+    assert rep["fallback"] == 0 and rep["nonempty_buckets"] >= 4
+
+
+def test_learned_half_buffer_edges_and_ram():
+    need_gpu()
+    import paper_2402_01816_gb300 as g
+    alpha = inputs.edge_alphabet()
+    rng = np.random.default_rng(22)
+    keys = np.concatenate([alpha[rng.integers(0, alpha.size, N_HALF // 2)], rng.normal(size=N_HALF - N_HALF // 2)])
+    assert _learned(keys, order=0, buffer_fraction=0.75)["fallback"] == 0
+    assert _learned(keys, order=1, with_payload=False, buffer_fraction=0.5)["fallback"] == 0
+    assert _learned(np.full(N_HALF + 1, -2.5), buffer_fraction=0.5)["fallback"] == 0   # one value, odd n
+    # below a half buffer the call is the plain (Frogsort2) sort
+    assert _learned(inputs.make_keys("mixture", N_HALF, seed=23), buffer_fraction=0.4)["fallback"] == 1
 
 
 def test_network_gain_over_first_stage():
