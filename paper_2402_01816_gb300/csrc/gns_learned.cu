@@ -937,12 +937,72 @@ struct LearnScratch {
     uint32_t* counts;   // 64 x ceil(n / PART_TILE)
 };
 
+// Phases 1 and 2 of the learned sort into the small workspace `ws`: sample
+// and sort 2^16 keys, fit the network, and derive the splitters and the
+// key -> bucket-range table (LearnLayout's spl, table and meta).
+int learn_fit_phase(const uint64_t* keys, int64_t n, int mode, const gns_learned_params& prm, char* ws,
+                    const LearnLayout& lay, cudaStream_t s)
+{
+    uint64_t* sample = (uint64_t*)(ws + lay.sample);
+    float* x = (float*)(ws + lay.x);
+    float* t = (float*)(ws + lay.t);
+    float* params0 = (float*)(ws + lay.params);
+    float* params1 = params0 + NP;
+    float* F = (float*)(ws + lay.F);
+    uint64_t* spl = (uint64_t*)(ws + lay.spl);
+    uint16_t* table = (uint16_t*)(ws + lay.table);
+    uint64_t* spl_raw = (uint64_t*)(ws + lay.spl_raw);
+    LearnMeta* meta = (LearnMeta*)(ws + lay.meta);
+    float* loss = (float*)(ws + lay.loss);
+    const int sms = sms_now();
+    float hp[NP];
+    init_params_host(hp);
+    const float* trained = params0;
+#define FTRY(x)                         \
+    do {                                \
+        if ((x) != cudaSuccess) return GNS_ERR_CUDA; \
+    } while (0)
+    // 1. sample, sort it, fit the network
+    FTRY(cudaMemcpyAsync(params0, hp, NP * sizeof(float), cudaMemcpyHostToDevice, s));
+    FTRY(cudaMemsetAsync(loss, 0, 256, s));
+    FTRY(launch(K_LEARN_SAMPLE, sample_kernel, dim3(SAMPLE_M / 256), dim3(256), 0, s, keys, n,
+                sample));
+    {
+        const int rs = sort_device(sample, nullptr, SAMPLE_M, mode, 1.0, s);
+        if (rs != GNS_OK) return rs;
+    }
+    FTRY(launch(K_LEARN_SAMPLE, fit_meta_kernel, dim3(1), dim3(128), 0, s, (const uint64_t*)sample, mode, meta));
+    FTRY(launch(K_LEARN_SAMPLE, fit_inputs_kernel, dim3(SAMPLE_M / 256), dim3(256), 0, s, (const uint64_t*)sample,
+                mode, x, t, (const LearnMeta*)meta));
+    if (prm.train_steps > 0) {
+        FTRY(launch(K_LEARN_FIT, mlp_train_kernel, dim3(FIT_CTAS), dim3(FIT_THREADS), sizeof(FitSmem), s,
+                    (const float*)x, (const float*)t, (int64_t)SAMPLE_M, (const float*)params0, params1, loss,
+                    prm.train_steps, prm.batch, prm.learning_rate));
+        trained = params1;
+    }
+    // 2. splitters and the key -> bucket-range table
+    FTRY(launch(K_LEARN_SPLIT, grid_eval_kernel, dim3(256), dim3(256), 0, s,
+                prm.train_steps > 0 ? trained : (const float*)nullptr, F));
+    FTRY(launch(K_LEARN_SPLIT, running_max_kernel, dim3(1), dim3(1024), 0, s, F));
+    FTRY(launch(K_LEARN_SPLIT, splitter_kernel, dim3(cdiv(NSPLIT, 256)), dim3(256), 0, s, (const float*)F, meta,
+                spl_raw));
+    FTRY(launch(K_LEARN_SPLIT, isolate_masses_kernel, dim3(cdiv(NSPLIT, 256)), dim3(256), 0, s,
+                (const uint64_t*)spl_raw, spl, meta));
+    FTRY(launch(K_LEARN_SPLIT, table_kernel, dim3((unsigned)(sms * 4)), dim3(256), 0, s, (const uint64_t*)spl,
+                (const LearnMeta*)meta, table));
+#undef FTRY
+    return GNS_OK;
+}
+
 }  // namespace
 
 // The learned sort on the device (all checks done by the caller).  xs: scratch
-// provided by the caller (nullptr: allocated here).
+// provided by the caller (nullptr: allocated here).  fitted: the small
+// workspace of an earlier learn_fit_phase whose splitters and table this call
+// uses instead of fitting its own (nullptr: fit here).
 int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, const gns_learned_params& prm,
-                        gns_learned_report* rep, cudaStream_t s, const LearnScratch* xs = nullptr)
+                        gns_learned_report* rep, cudaStream_t s, const LearnScratch* xs = nullptr,
+                        const char* fitted = nullptr)
 {
     learn_init_attributes();
     const LearnLayout lay = learn_layout(n, vals != nullptr);
@@ -960,15 +1020,8 @@ int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, con
     uint64_t* bufk = xs ? xs->bufk : (uint64_t*)(big + lay.bufk);
     uint32_t* bufv = vals ? (xs ? xs->bufv : (uint32_t*)(big + lay.bufv)) : nullptr;
     uint32_t* counts = xs ? xs->counts : (uint32_t*)(big + lay.counts);
-    uint64_t* sample = (uint64_t*)(ws + lay.sample);
-    float* x = (float*)(ws + lay.x);
-    float* t = (float*)(ws + lay.t);
-    float* params0 = (float*)(ws + lay.params);
-    float* params1 = params0 + NP;
-    float* F = (float*)(ws + lay.F);
     uint64_t* spl = (uint64_t*)(ws + lay.spl);
     uint16_t* table = (uint16_t*)(ws + lay.table);
-    uint64_t* spl_raw = (uint64_t*)(ws + lay.spl_raw);
     LearnMeta* meta = (LearnMeta*)(ws + lay.meta);
     unsigned long long* rowtot = (unsigned long long*)(ws + lay.rowtot);
     unsigned long long* btot = (unsigned long long*)(ws + lay.btot);
@@ -983,9 +1036,6 @@ int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, con
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     if (rep)
         for (auto& e : ev) cudaEventCreate(&e);
-    float hp[NP];
-    init_params_host(hp);
-    const float* trained = params0;
 #define LTRY(x)                     \
     do {                            \
         if ((x) != cudaSuccess) {   \
@@ -994,33 +1044,17 @@ int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, con
         }                           \
     } while (0)
     if (rep) LTRY(cudaEventRecord(ev[0], s));
-    // 1. sample, sort it, fit the network
-    LTRY(cudaMemcpyAsync(params0, hp, NP * sizeof(float), cudaMemcpyHostToDevice, s));
-    LTRY(cudaMemsetAsync(loss, 0, 256, s));
-    LTRY(launch(K_LEARN_SAMPLE, sample_kernel, dim3(SAMPLE_M / 256), dim3(256), 0, s, (const uint64_t*)keys, n,
-                sample));
-    rc = sort_device(sample, nullptr, SAMPLE_M, mode, 1.0, s);
-    if (rc != GNS_OK) goto done;
-    LTRY(launch(K_LEARN_SAMPLE, fit_meta_kernel, dim3(1), dim3(128), 0, s, (const uint64_t*)sample, mode, meta));
-    LTRY(launch(K_LEARN_SAMPLE, fit_inputs_kernel, dim3(SAMPLE_M / 256), dim3(256), 0, s, (const uint64_t*)sample,
-                mode, x, t, (const LearnMeta*)meta));
-    if (prm.train_steps > 0) {
-        LTRY(launch(K_LEARN_FIT, mlp_train_kernel, dim3(FIT_CTAS), dim3(FIT_THREADS), sizeof(FitSmem), s,
-                    (const float*)x, (const float*)t, (int64_t)SAMPLE_M, (const float*)params0, params1, loss,
-                    prm.train_steps, prm.batch, prm.learning_rate));
-        trained = params1;
+    if (fitted) {
+        // the fit of an earlier call: its splitters and table, a copy of its meta
+        spl = (uint64_t*)(fitted + lay.spl);
+        table = (uint16_t*)(fitted + lay.table);
+        LTRY(cudaMemcpyAsync(meta, fitted + lay.meta, sizeof(LearnMeta), cudaMemcpyDeviceToDevice, s));
+        LTRY(cudaMemcpyAsync(loss, fitted + lay.loss, sizeof(float), cudaMemcpyDeviceToDevice, s));
+    } else {
+        rc = learn_fit_phase((const uint64_t*)keys, n, mode, prm, ws, lay, s);
+        if (rc != GNS_OK) goto done;
     }
     if (rep) LTRY(cudaEventRecord(ev[1], s));
-    // 2. splitters, table, two stable 64-way passes
-    LTRY(launch(K_LEARN_SPLIT, grid_eval_kernel, dim3(256), dim3(256), 0, s,
-                prm.train_steps > 0 ? trained : (const float*)nullptr, F));
-    LTRY(launch(K_LEARN_SPLIT, running_max_kernel, dim3(1), dim3(1024), 0, s, F));
-    LTRY(launch(K_LEARN_SPLIT, splitter_kernel, dim3(cdiv(NSPLIT, 256)), dim3(256), 0, s, (const float*)F, meta,
-                spl_raw));
-    LTRY(launch(K_LEARN_SPLIT, isolate_masses_kernel, dim3(cdiv(NSPLIT, 256)), dim3(256), 0, s,
-                (const uint64_t*)spl_raw, spl, meta));
-    LTRY(launch(K_LEARN_SPLIT, table_kernel, dim3((unsigned)(sms * 4)), dim3(256), 0, s, (const uint64_t*)spl,
-                (const LearnMeta*)meta, table));
     LTRY(cudaMemsetAsync(btot, 0, NBUCKETS * 8, s));
 
     {
@@ -1262,6 +1296,17 @@ int learned_half_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode
     HalfNodes hn;
     for (int i = 0; i < 7; ++i) hn.x[i] = P.nodes[i];
     if (rep) memset(rep, 0, sizeof(*rep));
+    // one fit on a sample of the whole array serves all four leaves
+    const LearnLayout flay = learn_layout(n, vals != nullptr);
+    char* fitws = (char*)ws_alloc(flay.total, s);
+    cudaEvent_t fev[2] = {nullptr, nullptr};
+    if (!fitws) {
+        ws_free(ws, s);
+        return GNS_ERR_OOM;
+    }
+    learn_init_attributes();
+    if (rep)
+        for (auto& e : fev) cudaEventCreate(&e);
 #define HTRY(x)                     \
     do {                            \
         if ((x) != cudaSuccess) {   \
@@ -1270,6 +1315,14 @@ int learned_half_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode
         }                           \
     } while (0)
     HTRY(cudaMemsetAsync(ctl, 0, 256, s));
+    if (rep) HTRY(cudaEventRecord(fev[0], s));
+    rc = learn_fit_phase(keys, n, mode, prm, fitws, flay, s);
+    if (rc != GNS_OK) goto done;
+    if (rep) {
+        HTRY(cudaEventRecord(fev[1], s));
+        HTRY(cudaEventSynchronize(fev[1]));
+        cudaEventElapsedTime(&rep->fit_ms, fev[0], fev[1]);
+    }
     for (int j = 3; j >= 0; --j) {
         const HalfLeaf& L = P.leaf[j];
         LearnScratch xs;
@@ -1280,7 +1333,7 @@ int learned_half_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode
         xs.counts = (uint32_t*)at(L.counts);
         gns_learned_report lr;
         rc = learned_sort_device(keys + L.src, vals ? vals + L.src : nullptr, L.m, mode, prm, rep ? &lr : nullptr, s,
-                                 &xs);
+                                 &xs, fitws);
         if (rc != GNS_OK) goto done;
         if (rep) {
             rep->nonempty_buckets += lr.nonempty_buckets;
@@ -1299,7 +1352,10 @@ int learned_half_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode
     rc = frog_levels_device(sl, (const FrogNode*)nodes, 2, mode, ctl, ws + o_levels, s);
 #undef HTRY
 done:
+    ws_free(fitws, s);
     ws_free(ws, s);
+    if (rep)
+        for (auto& e : fev) cudaEventDestroy(e);
     return rc;
 }
 
@@ -1320,7 +1376,8 @@ size_t learned_workspace_bytes(int64_t n, double bf)
                              sort_workspace_bytes(SAMPLE_M, 1.0);
             leaf = x > leaf ? x : leaf;
         }
-        return half_main_bytes(P, true, &o_bufv, &o_nodes, &o_levels) + leaf;
+        // + the shared fit's small workspace, held for the whole call
+        return half_main_bytes(P, true, &o_bufv, &o_nodes, &o_levels) + learn_layout(n, true).total + leaf;
     }
     return sort_workspace_bytes(n, bf);
 }

@@ -194,10 +194,20 @@ __device__ __forceinline__ int2 frog_dep_range(int64_t c, const FrogNode& x, con
 // items[tk] for every ticket tk of a level (after the partition, before the
 // merge): ticket tk = base(k) + local (frog_locate) is chunk c = nchk - 1 -
 // local of a data-left node k and chunk c = local of a data-right one.
+//
+// skip_identity: a chunk whose outputs all come from one run and already sit
+// in their output slots (the leading left-run chunks of a data-left node, the
+// trailing right-run chunks of a data-right node, when the runs do not
+// overlap) becomes an empty item -- no load, no store.  This is the
+// symmetric merge's adaptivity to presorted data ("Symmetric merging"
+// section: at most half the data moves).  Such a chunk's inputs are its own
+// output slots, which no other chunk writes, so no chunk waits on it.  Off on
+// the level that decodes the keys, where every element is rewritten.
 static __global__ void frog_items_kernel(const FrogNode* __restrict__ level, const FrogNode* __restrict__ child,
                                          int64_t nnodes, int64_t nch, const int64_t* __restrict__ cstart,
                                          int64_t total, const int64_t* __restrict__ splits,
-                                         FrogItem* __restrict__ items, int* call_err, const int* presorted)
+                                         FrogItem* __restrict__ items, int* call_err, const int* presorted,
+                                         int skip_identity)
 {
     const int64_t tk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (tk >= total || skip_all(presorted)) return;
@@ -226,10 +236,15 @@ static __global__ void frog_items_kernel(const FrogNode* __restrict__ level, con
             it.ra = frog_data_slot(L) + a0;
             it.rb = frog_data_slot(R) + (w0 - a0);
             it.oslot = frog_data_slot(x) + w0;
-            const int2 r = frog_dep_range(c, x, L, R, sp, CHUNK);
-            if (r.x <= r.y) {
-                it.dep_lo = (int32_t)(x.side == 0 ? base + nchk - 1 - r.y : base + r.x);
-                it.dep_hi = (int32_t)(x.side == 0 ? base + nchk - 1 - r.x : base + r.y);
+            const bool identity = (nb == 0 && it.ra == it.oslot) || (na == 0 && it.rb == it.oslot);
+            if (skip_identity && identity) {
+                it.na = it.nb = 0;
+            } else {
+                const int2 r = frog_dep_range(c, x, L, R, sp, CHUNK);
+                if (r.x <= r.y) {
+                    it.dep_lo = (int32_t)(x.side == 0 ? base + nchk - 1 - r.y : base + r.x);
+                    it.dep_hi = (int32_t)(x.side == 0 ? base + nchk - 1 - r.x : base + r.y);
+                }
             }
         }
     }

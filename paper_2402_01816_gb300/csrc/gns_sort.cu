@@ -451,7 +451,7 @@ int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, 
                            s, sl, level, child, nnodes, (int64_t)0, cs, total, splits, skip));
             GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel, dim3((unsigned)ceil_div(total, 256)), dim3(256), 0, s,
                            level, child, nnodes, (int64_t)0, cs, total, (const int64_t*)splits, items, call_err,
-                           skip));
+                           skip, (int)(d != 0)));
             GNS_TRY(launch_frog_level(sl, (const FrogItem*)items, total, mode, (int)(d == 0), tickets + d, lflags,
                                       D - d, call_err, limit, skip_ticket, skip, s));
             skip_ticket = -1;
@@ -513,7 +513,7 @@ int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, 
                            splits, skip));
             GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel, dim3((unsigned)ceil_div(nnodes * nch, 256)),
                            dim3(256), 0, s, level, child, nnodes, nch, (const int64_t*)nullptr, nnodes * nch,
-                           (const int64_t*)splits, items, call_err, skip));
+                           (const int64_t*)splits, items, call_err, skip, (int)(d != 0)));
             GNS_TRY(launch_frog_level(sl, (const FrogItem*)items, nnodes * nch, mode, (int)(d == 0), tickets + d,
                                       lflags, D - d, call_err, limit, skip_ticket, skip, s));
             skip_ticket = -1;
@@ -563,7 +563,7 @@ int frog_levels_device(const Slots& sl, const FrogNode* nodes, int D, int mode, 
                        skip));
         GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel, dim3((unsigned)ceil_div(nnodes * nch, 256)), dim3(256), 0,
                        s, level, child, nnodes, nch, (const int64_t*)nullptr, nnodes * nch, (const int64_t*)splits,
-                       items, call_err, skip));
+                       items, call_err, skip, (int)(d != 0)));
         GNS_TRY(launch_frog_level(sl, (const FrogItem*)items, nnodes * nch, mode, (int)(d == 0), tickets + d, flags,
                                   D - d, call_err, limit, (int64_t)-1, skip, s));
     }
