@@ -44,6 +44,10 @@ static_assert(WS_CHUNK == CHUNK, "merge chunk size");
 // CTAs with 2048-output stages.
 template <int S>
 constexpr int ws_ctas_per_sm() { return WS_CONSUMERS == 128 ? (S <= 3 ? 6 : 4) : (S == 2 ? 3 : 2); }
+// The in-place level has no out buffer: three of its 3-stage CTAs still fit an
+// SM (3 x 74 KB of stages).
+template <int S>
+constexpr int ws_frog_ctas_per_sm() { return WS_CONSUMERS == 128 ? (S <= 3 ? 6 : 4) : (S <= 3 ? 3 : 2); }
 
 template <int C, int S>
 struct WsSmem {
@@ -724,7 +728,7 @@ __global__ void __launch_bounds__(WS_CONSUMERS + 32, ws_ctas_per_sm<S>())
 }
 
 template <int S>
-__global__ void __launch_bounds__(WS_CONSUMERS + 32, ws_ctas_per_sm<S>())
+__global__ void __launch_bounds__(WS_CONSUMERS + 32, ws_frog_ctas_per_sm<S>())
     frog_merge_ws_kernel(Slots sl, const FrogItem* __restrict__ items, int64_t total, int mode, int decode_out,
                          int* ticket, int* loaded, int epoch, int* call_err, uint64_t limit_ns, int64_t skip_ticket,
                          const int* presorted)
