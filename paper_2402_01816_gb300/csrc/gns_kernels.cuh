@@ -68,40 +68,6 @@ __device__ __forceinline__ int64_t merge_path(int64_t diag, int64_t na, int64_t 
     return lo;
 }
 
-// merge_path by a G-ary search: the G lanes of an aligned G-lane group of the
-// warp (all with the same arguments) probe G points of the remaining range at
-// once, so the range shrinks by a factor G + 1 per step (about 9 steps instead
-// of 27 for runs of 2^27 with G = 8).  The predicate "A[i] <= B[diag-1-i]"
-// holds exactly for i below the answer, so the lanes whose probe holds form a
-// prefix, and their count c places the answer after probe c-1 and at or
-// before probe c.  Every lane returns the answer.
-template <int G>
-__device__ __forceinline__ unsigned group_mask()
-{
-    static_assert(G >= 2 && G <= 32 && (G & (G - 1)) == 0, "group size");
-    return G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
-}
-
-template <int G, typename GA, typename GB>
-__device__ __forceinline__ int64_t merge_path_group(int64_t diag, int64_t na, int64_t nb, GA A, GB B)
-{
-    const int gl = threadIdx.x & (G - 1);
-    const unsigned gmask = group_mask<G>();
-    int64_t lo = imax64(0, diag - nb), hi = imin64(diag, na);
-    while (lo < hi) {
-        const int64_t len = hi - lo;
-        const int64_t p = lo + (len * (gl + 1)) / (G + 1);
-        const bool t = A(p) <= B(diag - 1 - p);
-        const int c = __popc(__ballot_sync(gmask, t));
-        const int64_t nlo = c > 0 ? lo + (len * c) / (G + 1) + 1 : lo;
-        const int64_t nhi = c < G ? lo + (len * (c + 1)) / (G + 1) : hi;
-        lo = nlo;
-        hi = nhi;
-    }
-    return lo;
-}
-constexpr int PART_G = 8;   // lanes per co-rank search in the partition kernels
-
 // Serial stable merge of ITEMS outputs from shared-memory runs [i, ie) and
 // [j, je) into registers.  Reads past the end are clamped to `last`.
 template <int N, int ITEMS>
@@ -327,25 +293,6 @@ static __global__ void merge_partition_kernel(const uint64_t* __restrict__ k, in
                            [&](int64_t x) { return B[x]; });
 }
 
-// The same splits, PART_G lanes per chunk (merge_path_group): launch
-// nblocks * PART_G threads in blocks of a multiple of 32.
-static __global__ void merge_partition_g_kernel(const uint64_t* __restrict__ k, int64_t n, int64_t w,
-                                                int64_t nblocks, int64_t* splits, const int* presorted)
-{
-    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / PART_G;
-    if (b >= nblocks) return;                                            // the whole group
-    if (__any_sync(group_mask<PART_G>(), skip_all(presorted))) return;   // uniform over the group
-    const int64_t out0 = b * CHUNK;
-    const int64_t ps = (out0 / (2 * w)) * (2 * w);
-    const int64_t lenA = imin64(w, n - ps);
-    const int64_t lenB = imax64(0, imin64(w, n - ps - w));
-    const uint64_t* A = k + ps;
-    const uint64_t* B = k + ps + lenA;
-    const int64_t r = merge_path_group<PART_G>(out0 - ps, lenA, lenB, [&](int64_t x) { return A[x]; },
-                                               [&](int64_t x) { return B[x]; });
-    if ((threadIdx.x & (PART_G - 1)) == 0) splits[b] = r;
-}
-
 // ---------------------------------------------------------------------------
 // <= 50% tier: the Frogsort1 layout
 // ---------------------------------------------------------------------------
@@ -504,25 +451,21 @@ __device__ __forceinline__ void frog_locate(int64_t idx, const int64_t* __restri
     nchk = cstart[k + 1] - base;
 }
 
-// splits[base(k) + c] = co-rank (left-run elements) of output c*CHUNK of node k;
-// PART_G lanes per chunk (merge_path_group): launch total * PART_G threads in
-// blocks of a multiple of 32.
+// splits[base(k) + c] = co-rank (left-run elements) of output c*CHUNK of node k.
 static __global__ void frog_partition_kernel(Slots sl, const FrogNode* __restrict__ level,
                                       const FrogNode* __restrict__ child, int64_t nnodes, int64_t nch,
                                       const int64_t* __restrict__ cstart, int64_t total, int64_t* splits,
                                       const int* presorted)
 {
-    const int64_t idx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / PART_G;
-    if (idx >= total) return;                                            // the whole group
-    if (__any_sync(group_mask<PART_G>(), skip_all(presorted))) return;   // uniform over the group
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total || skip_all(presorted)) return;
     int64_t k, c, base, nchk;
     frog_locate(idx, cstart, nnodes, nch, k, c, base, nchk);
     FrogNode x = level[k], L = child[2 * k], R = child[2 * k + 1];
     int64_t diag = imin64(c * CHUNK, x.n);
     int64_t ra = frog_data_slot(L), rb = frog_data_slot(R);
-    const int64_t r = merge_path_group<PART_G>(diag, L.n, R.n, [&](int64_t i) { return *sl.kp(ra + i); },
-                                               [&](int64_t j) { return *sl.kp(rb + j); });
-    if ((threadIdx.x & (PART_G - 1)) == 0) splits[idx] = r;
+    splits[idx] = merge_path(diag, L.n, R.n, [&](int64_t i) { return *sl.kp(ra + i); },
+                             [&](int64_t j) { return *sl.kp(rb + j); });
 }
 
 // One in-place symmetric merge level (kernel: frog_merge_tma_kernel).  A

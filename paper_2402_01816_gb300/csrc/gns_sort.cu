@@ -462,7 +462,7 @@ int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, 
             const FrogNode* level = internal + f0;
             const FrogNode* child = children + 2 * f0;
             const int64_t* cs = cstart + c0;
-            GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel, dim3((unsigned)ceil_div(total * PART_G, 256)), dim3(256), 0,
+            GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel, dim3((unsigned)ceil_div(total, 256)), dim3(256), 0,
                            s, sl, level, child, nnodes, (int64_t)0, cs, total, splits, skip));
             GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel, dim3((unsigned)ceil_div(total, 256)), dim3(256), 0, s,
                            level, child, nnodes, (int64_t)0, cs, total, (const int64_t*)splits, items, call_err,
@@ -487,7 +487,7 @@ int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, 
         const int64_t nblocks = ceil_div(n, CHUNK);
         for (int lvl = 0; lvl < L; ++lvl) {
             const int64_t w = (int64_t)TILE << lvl;
-            GNS_TRY(launch(K_MERGE_PARTITION, merge_partition_g_kernel, dim3((unsigned)ceil_div(nblocks * PART_G, 256)),
+            GNS_TRY(launch(K_MERGE_PARTITION, merge_partition_kernel, dim3((unsigned)ceil_div(nblocks, 256)),
                            dim3(256), 0, s, (const uint64_t*)cur_k, n, w, nblocks, splits, skip));
             GNS_TRY(launch_plain_level((const uint64_t*)cur_k, (const uint32_t*)cur_v, oth_k, oth_v, n, w, nblocks,
                                        (const int64_t*)splits, mode, (int)(lvl == L - 1), call_err, wait_limit_ns(),
@@ -523,7 +523,7 @@ int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, 
             const int64_t nch = frog_chunks(n, d);
             const FrogNode* level = nodes + (nnodes - 1);
             const FrogNode* child = nodes + (2 * nnodes - 1);
-            GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel, dim3((unsigned)ceil_div(nnodes * nch * PART_G, 256)),
+            GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel, dim3((unsigned)ceil_div(nnodes * nch, 256)),
                            dim3(256), 0, s, sl, level, child, nnodes, nch, (const int64_t*)nullptr, nnodes * nch,
                            splits, skip));
             GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel, dim3((unsigned)ceil_div(nnodes * nch, 256)),
@@ -573,7 +573,7 @@ int frog_levels_device(const Slots& sl, const FrogNode* nodes, int D, int mode, 
         const int64_t nch = frog_chunks(sl.n, d);
         const FrogNode* level = nodes + (nnodes - 1);
         const FrogNode* child = nodes + (2 * nnodes - 1);
-        GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel, dim3((unsigned)ceil_div(nnodes * nch * PART_G, 256)),
+        GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel, dim3((unsigned)ceil_div(nnodes * nch, 256)),
                        dim3(256), 0, s, sl, level, child, nnodes, nch, (const int64_t*)nullptr, nnodes * nch, splits,
                        skip));
         GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel, dim3((unsigned)ceil_div(nnodes * nch, 256)), dim3(256), 0,
