@@ -182,9 +182,9 @@ static __global__ void __launch_bounds__(256) run_detect_kernel(const uint64_t* 
         }
         asc = __syncthreads_and(asc);
         desc = __syncthreads_and(desc);
-        if (t == 0) {
-            if (!asc) atomicAnd(&presorted[0], 0);
-            if (!desc) atomicAnd(&presorted[1], 0);
+        if (t == 0) {   // clear a flag only while it is set: no atomic per tile on one word
+            if (!asc && ld_relaxed(&presorted[0])) atomicAnd(&presorted[0], 0);
+            if (!desc && ld_relaxed(&presorted[1])) atomicAnd(&presorted[1], 0);
         }
     }
 }
