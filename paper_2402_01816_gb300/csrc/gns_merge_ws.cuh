@@ -238,11 +238,33 @@ __device__ __forceinline__ void write_striped_shifted(uint64_t* ok, uint32_t* ov
     }
 }
 
-// Thread ct's m outputs to keys ok[shk + 8 ct ...] and payload ov[shv + 8 ct ...]:
-// 16-byte stores where the shift allows, narrower ones otherwise.
+// a[y] <- a[(y + r) mod N] (N a power of two, 0 <= r < N): log2(N) stages of
+// conditional fixed rotations, so no register is indexed at run time.
+template <int N, typename T>
+__device__ __forceinline__ void rotate_left(T (&a)[N], int r)
+{
+#pragma unroll
+    for (int sft = 1; sft < N; sft <<= 1) {
+        const bool on = (r & sft) != 0;
+        T tmp[N];
+#pragma unroll
+        for (int y = 0; y < N; ++y) tmp[y] = a[(y + sft) & (N - 1)];
+#pragma unroll
+        for (int y = 0; y < N; ++y) a[y] = on ? tmp[y] : a[y];
+    }
+}
+
+// Thread ct's m outputs to keys ok[shk + 8 ct ...] and payload ov[shv + 8 ct ...].
+// A full set of outputs is written one element per store in a rotated order:
+// at step y thread ct writes its element (y + r) mod 8, r = ct / 2 for keys
+// and ct / 4 for the payload.  Within a half-warp (8-byte keys) the 16
+// threads' slots ((8 ct + element) mod 16) are then all different, and so are
+// the 32 threads' payload banks ((8 ct + element) mod 32), whatever the shift:
+// no bank conflicts.  (Stores of a thread's 8 consecutive elements in element
+// order put every thread of a quarter- or half-warp on the same few banks.)
 template <int ITEMS>
 __device__ __forceinline__ void write_out_shifted(uint64_t* ok, uint32_t* ov, int shk, int shv,
-                                                  uint64_t (&kk)[ITEMS], const uint32_t (&v)[ITEMS], int m,
+                                                  uint64_t (&kk)[ITEMS], uint32_t (&v)[ITEMS], int m,
                                                   bool has_vals, int mode, int decode_out, int ct)
 {
     const int diag = ct * ITEMS;
@@ -251,28 +273,18 @@ __device__ __forceinline__ void write_out_shifted(uint64_t* ok, uint32_t* ov, in
         for (int x = 0; x < ITEMS; ++x) kk[x] = decode_key(kk[x], mode);
     }
     if (m == ITEMS) {
+        static_assert(ITEMS == 8, "rotated write-out assumes 8 outputs per thread");
         uint64_t* dk = ok + shk + diag;
-        if (shk == 0) {
+        const int rk = (ct >> 1) & 7;
+        rotate_left<ITEMS>(kk, rk);
 #pragma unroll
-            for (int x = 0; x < ITEMS; x += 2)
-                *reinterpret_cast<ulonglong2*>(dk + x) = make_ulonglong2(kk[x], kk[x + 1]);
-        } else {
-#pragma unroll
-            for (int x = 0; x < ITEMS; ++x) dk[x] = kk[x];
-        }
+        for (int y = 0; y < ITEMS; ++y) dk[(y + rk) & 7] = kk[y];
         if (has_vals) {
             uint32_t* dv = ov + shv + diag;
-            if (shv == 0) {
+            const int rv = (ct >> 2) & 7;
+            rotate_left<ITEMS>(v, rv);
 #pragma unroll
-                for (int x = 0; x < ITEMS; x += 4)
-                    *reinterpret_cast<uint4*>(dv + x) = make_uint4(v[x], v[x + 1], v[x + 2], v[x + 3]);
-            } else if (shv == 2) {
-#pragma unroll
-                for (int x = 0; x < ITEMS; x += 2) *reinterpret_cast<uint2*>(dv + x) = make_uint2(v[x], v[x + 1]);
-            } else {
-#pragma unroll
-                for (int x = 0; x < ITEMS; ++x) dv[x] = v[x];
-            }
+            for (int y = 0; y < ITEMS; ++y) dv[(y + rv) & 7] = v[y];
         }
     } else {
 #pragma unroll
