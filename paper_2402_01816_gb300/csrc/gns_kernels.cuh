@@ -156,7 +156,8 @@ __device__ void block_sort_smem(SmemKV<THREADS * ITEMS>& sm, int n_valid)
 // DETECT_TILE keys (one coalesced load per key, staged in shared memory with the
 // key before the tile) and stop as soon as both flags are cleared, so random
 // inputs cost about one wave.
-static __global__ void __launch_bounds__(256) run_detect_kernel(const uint64_t* __restrict__ keys, int64_t n,
+constexpr int DETECT_THREADS = 256;
+static __global__ void __launch_bounds__(DETECT_THREADS) run_detect_kernel(const uint64_t* __restrict__ keys, int64_t n,
                                                          int mode, int* presorted)
 {
     __shared__ uint64_t sk[DETECT_TILE + 1];
@@ -168,9 +169,20 @@ static __global__ void __launch_bounds__(256) run_detect_kernel(const uint64_t* 
         if (!s_go) return;
         const int64_t base = tile * DETECT_TILE;
         const int cnt = (int)imin64(DETECT_TILE, n - base);     // pairs (g-1, g) for g in [base, base+cnt)
-        for (int i = t; i <= cnt; i += blockDim.x) {
-            int64_t g = base - 1 + i;
-            sk[i] = g >= 0 ? encode_key(keys[g], mode) : 0;
+        // all of a thread's loads are issued before the first store (a loop that
+        // stores each load before issuing the next serialises the latencies)
+        constexpr int PER = DETECT_TILE / DETECT_THREADS + 1;
+        uint64_t r[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int i = t + q * DETECT_THREADS;
+            const int64_t g = base - 1 + i;
+            r[q] = (i <= cnt && g >= 0) ? keys[g] : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int i = t + q * DETECT_THREADS;
+            if (i <= cnt) sk[i] = base - 1 + i >= 0 ? encode_key(r[q], mode) : 0;
         }
         __syncthreads();
         bool asc = true, desc = true;
