@@ -215,15 +215,20 @@ static __global__ void reverse_kernel(uint64_t* keys, uint32_t* vals, int64_t n,
             const int64_t i0 = 4 * g, j0 = n - 4 - 4 * g;
             ulonglong2* fk = reinterpret_cast<ulonglong2*>(keys + i0);
             ulonglong2* bk = reinterpret_cast<ulonglong2*>(keys + j0);
+            uint4* fv = reinterpret_cast<uint4*>(vals + i0);
+            uint4* bv = reinterpret_cast<uint4*>(vals + j0);
+            // every load before the first store: one memory latency per group
             const ulonglong2 a01 = fk[0], a23 = fk[1], b01 = bk[0], b23 = bk[1];
+            uint4 x = make_uint4(0, 0, 0, 0), y = x;
+            if (vals) {
+                x = *fv;
+                y = *bv;
+            }
             fk[0] = make_ulonglong2(b23.y, b23.x);
             fk[1] = make_ulonglong2(b01.y, b01.x);
             bk[0] = make_ulonglong2(a23.y, a23.x);
             bk[1] = make_ulonglong2(a01.y, a01.x);
             if (vals) {
-                uint4* fv = reinterpret_cast<uint4*>(vals + i0);
-                uint4* bv = reinterpret_cast<uint4*>(vals + j0);
-                const uint4 x = *fv, y = *bv;
                 *fv = make_uint4(y.w, y.z, y.y, y.x);
                 *bv = make_uint4(x.w, x.z, x.y, x.x);
             }
