@@ -425,9 +425,12 @@ int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, 
 
     GNS_TRY(cudaMemsetAsync(ctl, 0, 256, s));
     GNS_TRY(cudaMemsetAsync(presorted, 1, 2 * sizeof(int), s));   // both flags "true"
-    GNS_TRY(launch(K_RUN_DETECT, run_detect_kernel, dim3((unsigned)imin(ceil_div(n, DETECT_TILE), 152 * 8)),
-                   dim3(256), 0, s,
-                   (const uint64_t*)keys, n, mode, presorted));
+    {
+        // one wave of persistent CTAs: a second partial wave would start its tiles late
+        static const int64_t detect_cap = resident_ctas(run_detect_kernel, DETECT_THREADS, 0);
+        GNS_TRY(launch(K_RUN_DETECT, run_detect_kernel, dim3((unsigned)imin(ceil_div(n, DETECT_TILE), detect_cap)),
+                       dim3(DETECT_THREADS), 0, s, (const uint64_t*)keys, n, mode, presorted));
+    }
     GNS_TRY(launch(K_REVERSE, reverse_kernel, dim3(152 * 8), dim3(256), 0, s, keys, vals, n, (const int*)presorted));
 
     if (n <= TILE) {
