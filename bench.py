@@ -553,6 +553,10 @@ def run_ours(args, ws, rank, local):
     if rank == 0 or ws > 1:
         hk = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
         hp = torch.empty(n, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+        for (p, bf) in combos[:2]:         # untimed: the workspace pool grows by the device copies once
+            np.copyto(hk, host[p])
+            np.copyto(hp, pay_host)
+            g.gns_sort_host(hk, hp, order=0, buffer_fraction=bf, stream=stream)
         e2e_times = []
         for _ in range(max(1, args.e2e_steps)):
             tot = 0.0
