@@ -121,13 +121,16 @@ __device__ void block_sort_smem(SmemKV<THREADS * ITEMS>& sm, int n_valid)
         }
     }
     for (int w = ITEMS; w < T && w < n_valid; w <<= 1) {
-        __syncthreads();
+        // while two runs span at most one warp's 32 * ITEMS positions, each
+        // warp reads only what its own threads wrote: a warp barrier suffices
+        const bool warp_local = 2 * w <= 32 * ITEMS;
+        if (warp_local) __syncwarp(); else __syncthreads();
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
             sm.k[pidx(t * ITEMS + j)] = k[j];
             sm.v[pidx(t * ITEMS + j)] = v[j];
         }
-        __syncthreads();
+        if (warp_local) __syncwarp(); else __syncthreads();
         const int gthreads = (2 * w) / ITEMS;
         const int a_beg = (t / gthreads) * 2 * w;
         const int b_beg = a_beg + w;
