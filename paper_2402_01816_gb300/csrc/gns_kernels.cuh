@@ -50,7 +50,7 @@ __device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
 
 template <int N>
 struct SmemKV {
-    uint64_t k[N + N / 16];
+    uint64_t k[N + N / 16 + 1];   // + 1: a serial merge may read the head one past its right run
     uint32_t v[N + N / 16];
 };
 
@@ -69,25 +69,29 @@ __device__ __forceinline__ int64_t merge_path(int64_t diag, int64_t na, int64_t 
 }
 
 // Serial stable merge of ITEMS outputs from shared-memory runs [i, ie) and
-// [j, je) into registers.  Reads past the end are clamped to `last`.
+// [j, je) into registers; the runs must hold at least ITEMS elements between
+// them.  The decision "take A" tests both bounds itself, so a run's head is
+// reloaded without a bounds test: past the end of run A it reads run B's
+// first element, past the end of run B at most one slot past the tile (the
+// spare slot of SmemKV), and the value is never used.
 template <int N, int ITEMS>
 __device__ __forceinline__ void serial_merge(const SmemKV<N>& sm, int i, int ie, int j, int je,
-                                             int last, uint64_t (&k)[ITEMS], uint32_t (&v)[ITEMS])
+                                             uint64_t (&k)[ITEMS], uint32_t (&v)[ITEMS])
 {
     uint64_t ka = i < ie ? sm.k[pidx(i)] : ~0ull;
     uint64_t kb = j < je ? sm.k[pidx(j)] : ~0ull;
 #pragma unroll
     for (int x = 0; x < ITEMS; ++x) {
-        bool takeA = (j >= je) || (i < ie && ka <= kb);
-        int src = takeA ? i : j;
+        const bool takeA = (j >= je) || (i < ie && ka <= kb);
+        const int src = takeA ? i : j;
         k[x] = takeA ? ka : kb;
-        v[x] = sm.v[pidx(src < last ? src : last)];
+        v[x] = sm.v[pidx(src)];
         if (takeA) {
             ++i;
-            ka = i < ie ? sm.k[pidx(i)] : ~0ull;
+            ka = sm.k[pidx(i)];
         } else {
             ++j;
-            kb = j < je ? sm.k[pidx(j)] : ~0ull;
+            kb = sm.k[pidx(j)];
         }
     }
 }
@@ -138,7 +142,7 @@ __device__ void block_sort_smem(SmemKV<THREADS * ITEMS>& sm, int n_valid)
         int ai = (int)merge_path(
             diag, w, w, [&](int64_t x) { return sm.k[pidx(a_beg + (int)x)]; },
             [&](int64_t x) { return sm.k[pidx(b_beg + (int)x)]; });
-        serial_merge<T, ITEMS>(sm, a_beg + ai, b_beg, b_beg + diag - ai, b_beg + w, T - 1, k, v);
+        serial_merge<T, ITEMS>(sm, a_beg + ai, b_beg, b_beg + diag - ai, b_beg + w, k, v);
     }
     __syncthreads();
 #pragma unroll
@@ -265,7 +269,7 @@ __device__ __forceinline__ bool skip_all(const int* ctl)
 // Sorts tile blockIdx.x of src (raw keys) into dst (encoded keys, or raw when
 // this is the only pass).  src == dst is allowed (each CTA owns its tile).
 template <int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS)   // <= 64 registers: 1024 threads per SM
     tile_sort_kernel(const uint64_t* src_k, const uint32_t* src_v, uint64_t* dst_k, uint32_t* dst_v,
                      int64_t n, int mode, int decode_out, const int* presorted)
 {
@@ -395,7 +399,7 @@ __device__ __forceinline__ int64_t find_leaf(const FrogNode* leaves, int64_t nle
 // once every overlapped leaf has published.  Earlier tickets never wait on later
 // ones, so the waits cannot deadlock; they are bounded anyway.
 template <int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS)   // <= 64 registers: 1024 threads per SM
     frog_setup_kernel(Slots sl, const FrogNode* __restrict__ leaves, int64_t nleaves, int mode,
                       int* ticket, int* loaded, int* call_err, uint64_t limit_ns,
                       const int* presorted)

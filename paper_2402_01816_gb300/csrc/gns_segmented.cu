@@ -124,7 +124,7 @@ __device__ __forceinline__ int64_t seg_of(const int64_t* prefix, int64_t nseg, i
 // Persistent: work item i of the row = tile (i - prefix[s]) of segment s.
 // big == 0: the row counts one tile per small segment (sorted whole).
 template <int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS)   // <= 64 registers: 1024 threads per SM
     seg_tile_kernel(uint64_t* keys, uint32_t* vals, uint64_t* bufk, uint32_t* bufv, const int64_t* __restrict__ off,
                     int64_t nseg, const int64_t* __restrict__ prefix, const uint8_t* __restrict__ levels, int mode,
                     const int* ctl)
