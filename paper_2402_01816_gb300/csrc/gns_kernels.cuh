@@ -139,10 +139,14 @@ __device__ void block_sort_smem(SmemKV<THREADS * ITEMS>& sm, int n_valid)
         const int a_beg = (t / gthreads) * 2 * w;
         const int b_beg = a_beg + w;
         const int diag = (t % gthreads) * ITEMS;
-        int ai = (int)merge_path(
-            diag, w, w, [&](int64_t x) { return sm.k[pidx(a_beg + (int)x)]; },
-            [&](int64_t x) { return sm.k[pidx(b_beg + (int)x)]; });
-        serial_merge<T, ITEMS>(sm, a_beg + ai, b_beg, b_beg + diag - ai, b_beg + w, k, v);
+        // merge path in 32-bit indices (both runs hold w elements)
+        int lo = diag - w > 0 ? diag - w : 0, hi = diag < w ? diag : w;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (sm.k[pidx(a_beg + mid)] <= sm.k[pidx(b_beg + diag - 1 - mid)]) lo = mid + 1;
+            else hi = mid;
+        }
+        serial_merge<T, ITEMS>(sm, a_beg + lo, b_beg, b_beg + diag - lo, b_beg + w, k, v);
     }
     __syncthreads();
 #pragma unroll

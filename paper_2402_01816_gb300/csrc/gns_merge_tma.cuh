@@ -95,7 +95,7 @@ __device__ __forceinline__ ChunkGeo merge_chunk_geo(int64_t b, int64_t n, int64_
 // ---------------------------------------------------------------- stages
 template <int C>
 struct InStage {
-    uint64_t k[C + 8];
+    uint64_t k[C + 10];   // + spare words: copies rounded out to 16 bytes, and heads read past a run
     uint32_t v[C + 16];
 };
 template <int C>

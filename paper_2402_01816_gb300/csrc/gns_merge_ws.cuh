@@ -188,17 +188,21 @@ __device__ __forceinline__ int merge_staged_ct(const InStage<C>& st, const Stage
     int i = lo, j = diag - lo;
     uint64_t ka = i < na ? st.k[g.ka + i] : ~0ull;
     uint64_t kb = j < nb ? st.k[g.kb + j] : ~0ull;
+    // "take A" tests both bounds itself, so a head is reloaded without a bounds
+    // test: past run A it reads at most ITEMS words past it (slice B or the
+    // stage's spare words: run A starts at word 0 or 1 and is shorter than C),
+    // past run B at most its next word.  Such a value is never used.
 #pragma unroll
     for (int x = 0; x < ITEMS; ++x) {
-        bool takeA = (j >= nb) || (i < na && ka <= kb);
+        const bool takeA = (j >= nb) || (i < na && ka <= kb);
         k[x] = takeA ? ka : kb;
         if (has_vals) v[x] = takeA ? st.v[g.va + (i < na ? i : na - 1)] : st.v[g.vb + (j < nb ? j : nb - 1)];
         if (takeA) {
             ++i;
-            ka = i < na ? st.k[g.ka + i] : ~0ull;
+            ka = st.k[g.ka + i];
         } else {
             ++j;
-            kb = j < nb ? st.k[g.kb + j] : ~0ull;
+            kb = st.k[g.kb + j];
         }
     }
     return cnt - diag < ITEMS ? cnt - diag : ITEMS;
