@@ -283,6 +283,17 @@ int gns_mlp_loss_grad(const float* params, const float* x, const float* t, int64
 int gns_mlp_train(const float* x, const float* t, int64_t m, const float* params_in, float* params_out,
                   float* loss_out, int steps, int batch, float learning_rate, gns_stream_t stream);
 
+/* Test hook: checks on the host the tree that gns_sort at this buffer_fraction
+ * in (0, 1) would run on for n keys (n > 8192): Frogsort1 at [0.5, 1), Frogsort2
+ * below ("Symmetric merging", "Frogsort1", "Frogsort2" sections).  Returns 0
+ * when every node's children split it exactly (sizes, buffers, adjoining
+ * regions and input ranges), every node has at least as many buffer slots as
+ * its inner child has elements, the leaves cover the input in order with at
+ * most one 8192-key tile each, every data slot lies inside the n + buffer
+ * slots, and the chunk numbering is consecutive; else the number (1-6) of the
+ * first invariant that fails; -1 for arguments outside that range. */
+int gns_frog_plan_check(int64_t n, double buffer_fraction);
+
 /* Test hook: 1 if gns_learned_sort at a buffer_fraction in [0.5, 1) takes its
  * half-buffer form for n keys, with and without a payload (the host-side
  * memory plan fits), else 0.  Runs on the host only. */

@@ -591,3 +591,88 @@ done:
 }
 
 }  // namespace gns
+
+// ------------------------------------------------------------ plan checks
+// Invariants of the trees the in-place tiers run on, checked on the host for a
+// test hook (gns_frog_plan_check).  Returns 0, or the number of the first
+// invariant that fails:
+//   1  children split the parent: sizes and buffers add up, regions adjoin;
+//   2  a node holds at least as many buffer slots as its inner child has
+//      elements (what the in-place merge needs, "Symmetric merging");
+//   3  left children are data-left, right children data-right, input ranges
+//      adjoin;
+//   4  the leaves, in input order, cover [0, n) without gaps and hold at most
+//      one tile each;
+//   5  every data slot range lies inside the slots [0, n + b);
+//   6  chunk numbering: each depth's node chunks are numbered consecutively.
+namespace gns {
+namespace {
+
+int check_split(const FrogNode& x, const FrogNode& L, const FrogNode& R, int64_t total)
+{
+    if (L.n + R.n != x.n || L.b + R.b != x.b || L.r != x.r || R.r != x.r + L.n + L.b) return 1;
+    if (L.n < 0 || R.n < 0 || L.b < 0 || R.b < 0) return 1;
+    const int64_t inner = x.side == 0 ? R.n : L.n;
+    if (x.b < inner) return 2;
+    if (L.side != 0 || R.side != 1 || L.s != x.s || R.s != x.s + L.n) return 3;
+    for (const FrogNode* c : {&L, &R})
+        if (frog_data_slot(*c) < 0 || frog_data_slot(*c) + c->n > total) return 5;
+    return 0;
+}
+
+int check_leaves(std::vector<FrogNode> leaves, int64_t n, int64_t total)
+{
+    std::sort(leaves.begin(), leaves.end(), [](const FrogNode& a, const FrogNode& b) { return a.s < b.s; });
+    int64_t next = 0;
+    for (const FrogNode& x : leaves) {
+        if (x.s != next || x.n > TILE) return 4;
+        if (frog_data_slot(x) < 0 || frog_data_slot(x) + x.n > total) return 5;
+        next += x.n;
+    }
+    return next == n ? 0 : 4;
+}
+
+}  // namespace
+}  // namespace gns
+
+extern "C" int gns_frog_plan_check(int64_t n, double buffer_fraction)
+{
+    using namespace gns;
+    if (n <= TILE || !(buffer_fraction > 0.0) || buffer_fraction >= 1.0) return -1;
+    if (buffer_fraction < 0.5) {
+        const int64_t pn = frog2_num(buffer_fraction);
+        const Frog2Plan P = frog2_plan(n, pn);
+        const int64_t total = n + n * pn / FROG2_DEN;
+        if (P.internal.empty() || P.internal[0].n != n || P.internal[0].r != 0 || P.internal[0].side != 0) return 1;
+        for (size_t k = 0; k < P.internal.size(); ++k) {
+            const int rc = check_split(P.internal[k], P.children[2 * k], P.children[2 * k + 1], total);
+            if (rc) return rc;
+        }
+        for (int d = 0; d < P.D; ++d) {
+            const int64_t f0 = P.first_node[d], nn = P.first_node[d + 1] - f0, c0 = P.first_cs[d];
+            if (P.cstart[c0] != 0) return 6;
+            for (int64_t k = 0; k < nn; ++k)
+                if (P.cstart[c0 + k + 1] - P.cstart[c0 + k] != ceil_div(P.internal[f0 + k].n, CHUNK)) return 6;
+        }
+        return check_leaves(P.leaves, n, total);
+    }
+    // Frogsort1: the node table the plan kernel builds, from the same split
+    const int D = frog_leaf_depth(n);
+    const int64_t total = n + n / 2;
+    std::vector<FrogNode> level(1), next, leaves;
+    level[0].n = n; level[0].b = n / 2; level[0].r = 0; level[0].s = 0; level[0].side = 0; level[0].pad = 0;
+    for (int d = 0; d < D; ++d) {
+        next.clear();
+        for (const FrogNode& x : level) {
+            FrogNode L, R;
+            frog_split(x, L, R);
+            const int rc = check_split(x, L, R, total);
+            if (rc) return rc;
+            if (ceil_div(x.n, CHUNK) > frog_chunks(n, d)) return 6;
+            next.push_back(L);
+            next.push_back(R);
+        }
+        level.swap(next);
+    }
+    return check_leaves(level, n, total);
+}

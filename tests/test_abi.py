@@ -145,3 +145,24 @@ def test_learned_half_buffer_ram(L, n):
     assert 1.0 + ws / (12.0 * n) < 1.52
     # a full buffer: the partition's 16 n bytes dominate
     assert nat.gns_workspace_bytes(n, 1.0, nat.WS_LEARNED) >= 16 * n
+
+
+@pytest.mark.parametrize("bf", [0.5, 0.75, 0.4, 0.25, 0.1, 1.0 / 64])
+def test_frog_plan_invariants(L, bf):
+    """The trees of the in-place tiers, built on the host by the library's own
+    split (Frogsort1) and planner (Frogsort2): children split each node
+    exactly, every node can hold its inner child in its buffer, the leaves
+    tile the input in order, every data slot lies in the n + buffer slots,
+    chunk numbering is consecutive.  Sizes near tile multiples, odd sizes,
+    and up to 2^31."""
+    import random
+    L.gns_frog_plan_check.argtypes = [ctypes.c_int64, ctypes.c_double]
+    L.gns_frog_plan_check.restype = ctypes.c_int
+    rng = random.Random(7)
+    T = 8192
+    sizes = [T + 1, 2 * T - 1, 2 * T, 2 * T + 1, 3 * T + 5, 37 * T + 11, (1 << 18) + 12345, (1 << 20) - 1]
+    sizes += [rng.randrange(T + 1, 1 << 26) for _ in range(40)]
+    sizes += [(1 << 27), (1 << 27) + 7, (1 << 31)] if bf >= 0.1 else [(1 << 27) + 7]
+    for n in sizes:
+        assert L.gns_frog_plan_check(n, bf) == 0, (n, bf)
+    assert L.gns_frog_plan_check(T, bf) == -1            # one tile: no tree
