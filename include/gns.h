@@ -24,6 +24,10 @@
  *   out) land in a per-device status word read by gns_stream_status().  With
  *   the environment variable GNS_SYNC_STATUS=1 every call synchronises its
  *   stream and returns that status itself.
+ * - Tuning knobs read once per process from the environment (results never
+ *   change, only speed): GNS_MERGE_PIPE=ws2|ws3|ws4 (stages of the 100% merge
+ *   levels; default ws2), GNS_FROG_PIPE=ws2|ws3|ws4 (the in-place levels;
+ *   default ws3), GNS_SEG_SCHEDULE (below).
  * - Workspace: the library allocates only its own scratch, through the
  *   allocator hook (gns_set_allocator; default cudaMallocAsync on `stream`) and
  *   frees it stream-ordered before returning.  gns_workspace_bytes() reports
