@@ -20,6 +20,12 @@ The oracle itself is plain C (``gns_oracle.c``), compiled with gcc into
                        of the Frogsort0 / Frogsort1 sections.
 * ``frogsort2``     -- Frogsort2 section: imbalanced split with inner fraction p
                        and floor(p n) buffer.
+* ``omitsort`` / ``octosort`` -- Full adaptivity section: merges omitted where
+                       the halves do not overlap; data-driven orientation with
+                       one final reversal (100% buffer).
+* ``geckosort`` / ``squidsort`` -- Symmetric merging and Squidsort sections:
+                       Frogsort1's layout with mirrored orientation per branch,
+                       or with the orientation decided by the data.
 * ``segmented_sort``, ``final_position``, ``compare``.
 """
 from __future__ import annotations
@@ -86,6 +92,10 @@ def _load():
             lib.orc_frog_depth.restype = i32
             lib.orc_frog_trace.argtypes = [i64, i32, P, i32]
             lib.orc_frog_trace.restype = i32
+            lib.orc_omitsort.argtypes = [P, P, i64, i32, i32, i32, P]
+            lib.orc_omitsort.restype = i32
+            lib.orc_symsort.argtypes = [P, P, i64, i32, i32, i32, P]
+            lib.orc_symsort.restype = i32
             _lib = lib
     return _lib
 
@@ -172,6 +182,58 @@ def frogsort2(keys: np.ndarray, payload: np.ndarray | None = None, order: int = 
         return keys, payload, {"setup_moves": int(ctr[0]), "merge_moves": int(ctr[1]),
                                "merge_compares": int(ctr[2])}
     return keys, payload
+
+
+def _omit(keys, payload, order, lazy, return_counters):
+    keys, payload = _prep(keys, payload)
+    ctr = np.zeros(2, dtype=np.int64)
+    rc = _load().orc_omitsort(_ptr(keys), _ptr(payload), keys.size, _key_type(keys), order, lazy, _ptr(ctr))
+    if rc:
+        raise MemoryError("oracle omitsort: allocation failed")
+    if return_counters:
+        return keys, payload, {"moves": int(ctr[0]), "compares": int(ctr[1])}
+    return keys, payload
+
+
+def omitsort(keys: np.ndarray, payload: np.ndarray | None = None, order: int = ASC,
+             return_counters: bool = False):
+    """Paper's Omitsort: merges of non-overlapping halves omitted, data location
+    returned by the recursion; counters (moves, comparisons)."""
+    return _omit(keys, payload, order, 0, return_counters)
+
+
+def octosort(keys: np.ndarray, payload: np.ndarray | None = None, order: int = ASC,
+             return_counters: bool = False):
+    """Paper's Octosort: Omitsort with data-driven orientation, the target
+    order enforced only where children disagree, one final reversal."""
+    return _omit(keys, payload, order, 1, return_counters)
+
+
+def _sym(keys, payload, order, lazy, return_counters):
+    keys, payload = _prep(keys, payload)
+    ctr = np.zeros(3, dtype=np.int64)
+    rc = _load().orc_symsort(_ptr(keys), _ptr(payload), keys.size, _key_type(keys), order, lazy, _ptr(ctr))
+    if rc:
+        raise MemoryError("oracle symmetric sort: allocation failed")
+    if return_counters:
+        return keys, payload, {"setup_moves": int(ctr[0]), "merge_moves": int(ctr[1]),
+                               "compares": int(ctr[2])}
+    return keys, payload
+
+
+def geckosort(keys: np.ndarray, payload: np.ndarray | None = None, order: int = ASC,
+              return_counters: bool = False):
+    """Paper's Geckosort (Frogsort1's layout, data-left nodes left-ascending,
+    data-right nodes right-ascending); counters (setup moves, merge moves,
+    comparisons)."""
+    return _sym(keys, payload, order, 0, return_counters)
+
+
+def squidsort(keys: np.ndarray, payload: np.ndarray | None = None, order: int = ASC,
+              return_counters: bool = False):
+    """Paper's Squidsort1 (Frogsort1 with Octosort's data-driven orientation and
+    a non-overlap test per node)."""
+    return _sym(keys, payload, order, 1, return_counters)
 
 
 def frog2_buffer(n: int, p_num: int, p_den: int) -> int:

@@ -602,3 +602,324 @@ int orc_frog_trace(int64_t n, int split_unit, int32_t* labels_out, int max_rows)
     free(dest);
     return D + 1;
 }
+
+/* ========================================================================
+ * Orientations ("Definition of sorting" chapter: the four stable API
+ * targets).  The adaptive sorts below let a node return its sorted data in
+ * either of two orientations: ORI_ASC is the target itself (AscLeft: keys in
+ * order from left to right, ties in input order); ORI_DESC is its mirror image
+ * (AscRight: the same sequence stored right to left).  A single element is
+ * both (ORI_ANY).  Element e (0-based, in AscLeft order) of a run of n stored
+ * at slot a in orientation o sits at slot a + e (ORI_ASC) or a + n - 1 - e
+ * (ORI_DESC).
+ * ======================================================================== */
+enum { ORI_ASC = 0, ORI_DESC = 1, ORI_ANY = 2 };
+
+static int64_t ori_slot(int ori, int64_t a, int64_t n, int64_t e)
+{
+    return ori == ORI_DESC ? a + n - 1 - e : a + e;
+}
+
+/* ------------------------------------------------------------------------
+ * Omitsort and Octosort ("Full adaptivity" section), 100% buffer.
+ *
+ * Omitsort: top-down mergesort (Knuthsort's split, left = floor(n/2)) over two
+ * regions, the caller's array (region 0) and an n-slot buffer (region 1).
+ * Instead of Nocopy's fixed alternation, every sort returns the region its
+ * data ended in.  If the two halves ended in different regions, the half in
+ * the buffer is copied to the data region first.  Then one comparison of the
+ * two elements at the halves' boundary decides whether they overlap; if not,
+ * the merge is omitted and the node stays where it is, else the halves are
+ * merged into the other region.  At the end the data is copied back if it
+ * lies in the buffer.  Presorted input costs n - 1 comparisons and no move.
+ *
+ * Octosort: Omitsort whose nodes return an orientation as well, decided by the
+ * data.  Two single elements take ORI_DESC when they are strictly out of
+ * order, else ORI_ASC (one comparison, no move).  Children of the same
+ * orientation (a single element adopts its sibling's) are tested for overlap
+ * in that orientation (ORI_ASC: left's last <= right's first; ORI_DESC: the
+ * left's last element strictly above the right's first, because the mirror
+ * image keeps the later of two equal keys on the left) and merged in it when
+ * they overlap.  Only when the children disagree is the desired order
+ * enforced: they are merged into ORI_ASC, the ORI_DESC child read from its
+ * far end.  A root in ORI_DESC is reversed once at the end, so strictly
+ * descending input costs n - 1 comparisons and one reversal.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    orc_ctx c;
+    int lazy;               /* 0 = Omitsort, 1 = Octosort */
+    uint64_t* k[2];
+    uint32_t* p[2];         /* NULL when there is no payload */
+} omit_run;
+
+typedef struct { int reg, ori; } omit_res;
+
+static void om_put(omit_run* f, int dr, int64_t d, int sr, int64_t s)
+{
+    f->k[dr][d] = f->k[sr][s];
+    if (f->p[0]) f->p[dr][d] = f->p[sr][s];
+    f->c.moves++;
+}
+
+/* Out-of-place merge of the runs [lo, lo+nl) (orientation oL) and
+ * [lo+nl, lo+n) (orientation oR) of region r into region 1-r, stored in
+ * orientation o.  Both runs are walked in AscLeft order; ties take the left
+ * run (stability); Knuth's single exhaustion check per step. */
+static void om_merge(omit_run* f, int r, int64_t lo, int64_t nl, int oL, int64_t nr, int oR, int o)
+{
+    const int kt = f->c.key_type, od = f->c.order;
+    const int64_t n = nl + nr;
+    int64_t i = 0, j = 0, t = 0;
+    const uint64_t* sk = f->k[r];
+    for (;;) {
+        int64_t a = ori_slot(oL, lo, nl, i), b = ori_slot(oR, lo + nl, nr, j);
+        f->c.compares++;
+        if (ord_cmp(sk[b], sk[a], kt, od) < 0) {
+            om_put(f, 1 - r, ori_slot(o, lo, n, t++), r, b);
+            if (++j == nr) {
+                for (; i < nl; i++) om_put(f, 1 - r, ori_slot(o, lo, n, t++), r, ori_slot(oL, lo, nl, i));
+                return;
+            }
+        } else {
+            om_put(f, 1 - r, ori_slot(o, lo, n, t++), r, a);
+            if (++i == nl) {
+                for (; j < nr; j++) om_put(f, 1 - r, ori_slot(o, lo, n, t++), r, ori_slot(oR, lo + nl, nr, j));
+                return;
+            }
+        }
+    }
+}
+
+static omit_res om_rec(omit_run* f, int64_t lo, int64_t n)
+{
+    omit_res res = {0, f->lazy ? ORI_ANY : ORI_ASC};
+    if (n == 1) return res;
+    const int64_t nl = n / 2, nr = n - nl, m = lo + nl;
+    omit_res a = om_rec(f, lo, nl), b = om_rec(f, m, nr);
+    if (a.reg != b.reg) {                 /* bring the half in the buffer to the data region */
+        if (a.reg == 1) for (int64_t e = lo; e < m; e++) om_put(f, 0, e, 1, e);
+        else            for (int64_t e = m; e < lo + n; e++) om_put(f, 0, e, 1, e);
+        a.reg = b.reg = 0;
+    }
+    const int r = a.reg, kt = f->c.key_type, od = f->c.order;
+    const uint64_t* k = f->k[r];
+    res.reg = r;
+    if (a.ori == ORI_ANY && b.ori == ORI_ANY) {       /* Octosort: two single elements */
+        f->c.compares++;
+        res.ori = ord_cmp(k[m], k[m - 1], kt, od) < 0 ? ORI_DESC : ORI_ASC;
+        return res;                                   /* in either orientation already */
+    }
+    const int oL = a.ori == ORI_ANY ? b.ori : a.ori;
+    const int oR = b.ori == ORI_ANY ? a.ori : b.ori;
+    if (oL != oR) {                                   /* disagreement: enforce the target */
+        om_merge(f, r, lo, nl, oL, nr, oR, ORI_ASC);
+        res.reg = 1 - r;
+        res.ori = ORI_ASC;
+        return res;
+    }
+    f->c.compares++;                                  /* the non-overlap test */
+    const int c = ord_cmp(k[m - 1], k[m], kt, od);
+    if (oL == ORI_ASC ? c <= 0 : c > 0) {
+        res.ori = oL;                                 /* omitted: no move */
+        return res;
+    }
+    om_merge(f, r, lo, nl, oL, nr, oR, oL);
+    res.reg = 1 - r;
+    res.ori = oL;
+    return res;
+}
+
+/* lazy = 0: Omitsort, 1: Octosort.  counters (may be NULL): [0] element moves
+ * (merges, region fix-up copies, the final copy or reversal), [1] comparisons.
+ * Returns 0, or -1 on allocation failure. */
+int orc_omitsort(uint64_t* keys, uint32_t* payload, int64_t n, int key_type, int order, int lazy,
+                 int64_t* counters)
+{
+    omit_run f;
+    memset(&f, 0, sizeof(f));
+    f.c.key_type = key_type; f.c.order = order; f.lazy = lazy ? 1 : 0;
+    if (n >= 2) {
+        f.k[0] = keys; f.p[0] = payload;
+        f.k[1] = (uint64_t*)malloc((size_t)n * sizeof(uint64_t));
+        f.p[1] = payload ? (uint32_t*)malloc((size_t)n * sizeof(uint32_t)) : NULL;
+        if (!f.k[1] || (payload && !f.p[1])) { free(f.k[1]); free(f.p[1]); return -1; }
+        omit_res res = om_rec(&f, 0, n);
+        if (res.ori == ORI_DESC) {                    /* the one final reversal */
+            if (res.reg == 1) {
+                for (int64_t e = 0; e < n; e++) om_put(&f, 0, e, 1, n - 1 - e);
+            } else {
+                for (int64_t i = 0, j = n - 1; i < j; i++, j--) {
+                    uint64_t tk = keys[i]; keys[i] = keys[j]; keys[j] = tk;
+                    if (payload) { uint32_t tp = payload[i]; payload[i] = payload[j]; payload[j] = tp; }
+                    f.c.moves += 2;
+                }
+            }
+        } else if (res.reg == 1) {
+            for (int64_t e = 0; e < n; e++) om_put(&f, 0, e, 1, e);
+        }
+        free(f.k[1]); free(f.p[1]);
+    }
+    if (counters) { counters[0] = f.c.moves; counters[1] = f.c.compares; }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Geckosort1 and Squidsort1: symmetric merging ("Symmetric merging" and
+ * "Squidsort" sections) on Frogsort1's tree, buffer and setup (frog_children,
+ * frog_setup_dest above), with nodes in either orientation.
+ *
+ * The in-place merge of a node (sym_merge) writes from the inner end of the
+ * node's output outward (data-left node: from slot r+n-1 down; data-right
+ * node: from slot r+b up) and reads each run from the end whose element is
+ * written first.  The outer child's run lies under the output, so it must be
+ * read from its inner end, which fixes the node's orientation to the outer
+ * child's; the inner child lies in the buffer, beyond the output, and can be
+ * read from either end, so its orientation is free.  With the orientation o
+ * of the node, the element written first is the largest and latest
+ * ("largest first") when a data-left node is ORI_ASC or a data-right node
+ * ORI_DESC, else the smallest and earliest ("smallest first").  Largest first
+ * takes the right run on ties (its elements are later in the input), smallest
+ * first takes the left run.  The merge stops when the inner child is used
+ * up: the rest of the outer child is then in its final slots.
+ *
+ * Geckosort1: every data-left node is ORI_ASC and every data-right node
+ * ORI_DESC (one branch sorted left-ascending, the other right-ascending, the
+ * right branch the mirror image of the left).  On ascending input a data-left
+ * node moves only its inner child and a data-right node moves everything; on
+ * descending input the other way round: 25% fewer moves for either order.
+ *
+ * Squidsort1: the orientation is decided by the data (Octosort's lazily
+ * enforced order): two single elements take ORI_DESC when they are strictly
+ * out of order (one comparison, which is also their non-overlap test); any
+ * larger node takes its outer child's orientation (the one the in-place merge
+ * can produce; a single element adopts its sibling's).  Every larger node
+ * first compares the inner child's last element in write order with the outer
+ * child's first (the non-overlap test); when the inner child comes entirely
+ * first it is moved next to the outer child without further comparisons.
+ * A root in ORI_DESC is reversed once at the end.  Presorted and strictly
+ * descending inputs cost one comparison per node and move half the elements
+ * per level (plus the one reversal for the latter).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    frog_run f;
+    int lazy;           /* 0 = Geckosort1, 1 = Squidsort1 */
+} sym_run;
+
+/* Slot of the t-th element of child x (orientation o) in write order. */
+static int64_t sym_slot(const frog_node* x, int o, int largest_first, int64_t t)
+{
+    const int64_t e = largest_first ? x->n - 1 - t : t;    /* position in AscLeft order */
+    return ori_slot(o, frog_data_slot(x), x->n, e);
+}
+
+static void sym_merge(sym_run* s, const frog_node* x, const frog_node* L, int oL, const frog_node* R, int oR,
+                      int o, int test_overlap)
+{
+    frog_run* f = &s->f;
+    const int kt = f->c.key_type, od = f->c.order;
+    const int lf = (x->side == 0) == (o == ORI_ASC);
+    int64_t w = x->side == 0 ? x->r + x->n - 1 : x->r + x->b;
+    const int64_t step = x->side == 0 ? -1 : 1;
+    const frog_node* I = x->side == 0 ? R : L;         /* inner child */
+    const frog_node* O = x->side == 0 ? L : R;         /* outer child */
+    const int oI = x->side == 0 ? oR : oL, oO = x->side == 0 ? oL : oR;
+    int64_t i = 0, j = 0;                               /* taken from L, from R */
+    /* element a of L goes before element b of R in write order */
+#define SYM_L_FIRST(a, b) (lf ? ord_cmp(f->k[a], f->k[b], kt, od) > 0 : ord_cmp(f->k[a], f->k[b], kt, od) <= 0)
+    if (test_overlap) {
+        const int64_t il = sym_slot(I, oI, lf, I->n - 1), of = sym_slot(O, oO, lf, 0);
+        f->c.compares++;
+        const int inner_first = x->side == 0 ? !SYM_L_FIRST(of, il) : SYM_L_FIRST(il, of);
+        if (inner_first) {
+            for (int64_t t = 0; t < I->n; t++, w += step) frog_move(f, w, sym_slot(I, oI, lf, t));
+            return;
+        }
+    }
+    while (x->side == 0 ? j < R->n : i < L->n) {
+        int take_l;
+        if (i == L->n) take_l = 0;
+        else if (j == R->n) take_l = 1;
+        else {
+            f->c.compares++;
+            take_l = SYM_L_FIRST(sym_slot(L, oL, lf, i), sym_slot(R, oR, lf, j));
+        }
+        if (take_l) frog_move(f, w, sym_slot(L, oL, lf, i++));
+        else        frog_move(f, w, sym_slot(R, oR, lf, j++));
+        w += step;
+    }
+#undef SYM_L_FIRST
+}
+
+static int sym_rec(sym_run* s, const frog_node* x)
+{
+    if (x->n == 1) return ORI_ANY;
+    frog_node L, R;
+    frog_children(x, 1, &L, &R);
+    int oL = sym_rec(s, &L), oR = sym_rec(s, &R);
+    if (!s->lazy) {                                     /* Geckosort1: orientation by side */
+        if (oL == ORI_ANY) oL = ORI_ASC;
+        if (oR == ORI_ANY) oR = ORI_DESC;
+        const int o = x->side == 0 ? ORI_ASC : ORI_DESC;
+        sym_merge(s, x, &L, oL, &R, oR, o, 0);
+        return o;
+    }
+    if (oL == ORI_ANY && oR == ORI_ANY) {               /* Squidsort1: the data decides */
+        const frog_run* f = &s->f;
+        s->f.c.compares++;
+        const int o = ord_cmp(f->k[frog_data_slot(&R)], f->k[frog_data_slot(&L)], f->c.key_type, f->c.order) < 0
+                          ? ORI_DESC : ORI_ASC;
+        /* the comparison also settles the order: the inner element is moved next to the outer one */
+        const frog_node* I = x->side == 0 ? &R : &L;
+        const int64_t w = x->side == 0 ? x->r + x->n - 1 : x->r + x->b;
+        frog_move(&s->f, w, frog_data_slot(I));
+        return o;
+    }
+    if (oL == ORI_ANY) oL = oR;
+    if (oR == ORI_ANY) oR = oL;
+    const int o = x->side == 0 ? oL : oR;               /* the outer child's orientation */
+    sym_merge(s, x, &L, oL, &R, oR, o, 1);
+    return o;
+}
+
+/* lazy = 0: Geckosort1, 1: Squidsort1; floor(n/2) buffer slots as Frogsort1.
+ * counters (may be NULL): [0] setup moves, [1] merge moves (including the
+ * final reversal), [2] comparisons.  Returns 0, or -1 on allocation failure. */
+int orc_symsort(uint64_t* keys, uint32_t* payload, int64_t n, int key_type, int order, int lazy,
+                int64_t* counters)
+{
+    int64_t setup_moves = 0;
+    sym_run s;
+    memset(&s, 0, sizeof(s));
+    s.f.c.key_type = key_type; s.f.c.order = order; s.f.g = 1; s.lazy = lazy ? 1 : 0;
+    if (n >= 2) {
+        int64_t b = n / 2, m = n + b;
+        s.f.k = (uint64_t*)malloc((size_t)m * sizeof(uint64_t));
+        s.f.p = payload ? (uint32_t*)malloc((size_t)m * sizeof(uint32_t)) : NULL;
+        int64_t* dest = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+        if (!s.f.k || (payload && !s.f.p) || !dest) { free(s.f.k); free(s.f.p); free(dest); return -1; }
+        memcpy(s.f.k, keys, (size_t)n * sizeof(uint64_t));
+        if (payload) memcpy(s.f.p, payload, (size_t)n * sizeof(uint32_t));
+        frog_node root = frog_root(n, 1);
+        frog_setup_dest(&root, 1, dest);
+        for (int64_t e = n - 1; e >= 0; e--) {          /* dest >= source, increasing: top down */
+            if (dest[e] != e) {
+                s.f.k[dest[e]] = s.f.k[e];
+                if (payload) s.f.p[dest[e]] = s.f.p[e];
+                setup_moves++;
+            }
+        }
+        free(dest);
+        if (sym_rec(&s, &root) == ORI_DESC) {           /* the root is data-left: slots [0, n) */
+            for (int64_t i = 0, j = n - 1; i < j; i++, j--) {
+                uint64_t tk = s.f.k[i]; s.f.k[i] = s.f.k[j]; s.f.k[j] = tk;
+                if (payload) { uint32_t tp = s.f.p[i]; s.f.p[i] = s.f.p[j]; s.f.p[j] = tp; }
+                s.f.c.moves += 2;
+            }
+        }
+        memcpy(keys, s.f.k, (size_t)n * sizeof(uint64_t));
+        if (payload) memcpy(payload, s.f.p, (size_t)n * sizeof(uint32_t));
+        free(s.f.k); free(s.f.p);
+    }
+    if (counters) { counters[0] = setup_moves; counters[1] = s.f.c.moves; counters[2] = s.f.c.compares; }
+    return 0;
+}

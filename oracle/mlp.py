@@ -15,8 +15,8 @@ it step by step:
 * its gradient (backpropagation written out by hand) -- pinned in the tests
   by central finite differences of the loss, which share no code with it;
 * one Adam step;
-* the normalisation of a key to the network input and the integer bucket
-  function defined by a splitter array (53-bit prefixes of the order map).
+* the integer bucket function defined by a splitter array: the number of
+  splitters at or below a key's 53-bit order-mapped prefix.
 
 The final result of the learned sort is the plain stable sort, so it is
 checked against ``oracle.stable_sort``, not against anything here.
@@ -87,11 +87,6 @@ def adam_step(p, g, m1, m2, step, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8):
     mh = m1 / (1 - beta1 ** step)
     vh = m2 / (1 - beta2 ** step)
     return p - lr * mh / (np.sqrt(vh) + eps), m1, m2
-
-
-def key53(keys_bits_encoded):
-    """53-bit prefix of order-mapped keys (the unit the bucket function works in)."""
-    return np.asarray(keys_bits_encoded, dtype=np.uint64) >> np.uint64(11)
 
 
 def buckets_from_splitters(e53, spl53):

@@ -39,6 +39,10 @@ SORTS = {
     "frogsort2_1/4": lambda k, p, o: oracle.frogsort2(k, p, o, p_num=1, p_den=4, leaf=1),
     "frogsort2_1/3_leaf2": lambda k, p, o: oracle.frogsort2(k, p, o, p_num=1, p_den=3, leaf=2),
     "frogsort2_1/8": lambda k, p, o: oracle.frogsort2(k, p, o, p_num=1, p_den=8, leaf=1),
+    "omitsort": lambda k, p, o: oracle.omitsort(k, p, o),
+    "octosort": lambda k, p, o: oracle.octosort(k, p, o),
+    "geckosort1": lambda k, p, o: oracle.geckosort(k, p, o),
+    "squidsort1": lambda k, p, o: oracle.squidsort(k, p, o),
 }
 
 
