@@ -150,24 +150,26 @@ int gns_segmented_sort_ex(void* keys, int key_type, uint32_t* payload,
  * (The paper has no counterpart: this is a service for callers, not a step of
  * the method.)
  *
- * Some callers cannot allocate device memory when they need a sort: code that
- * runs while somebody else is capturing a CUDA graph (an allocation there is
- * either illegal or becomes part of the graph), latency-critical or signal-safe
- * paths that forbid allocator calls, and hosts that own all device memory and
- * hand a library only the buffers it works on.  This entry point calls no
- * cudaMalloc, cudaFree, stream-ordered allocator or allocator hook.  Its
- * scratch is one fixed device array inside this library, sized for
- * GNS_NOALLOC_MAX_N elements (about 12 MiB); every GPU that loads the library
- * holds that array until the process exits.
+ * Some callers cannot allocate device memory when they need a sort: real-time
+ * or signal-safe paths where an allocator call (which may take a lock,
+ * synchronise the device or map memory) is not allowed, hosts that reserve all
+ * device memory up front and hand a library only the buffers it works on, and
+ * code under a fixed memory budget with no room for gns_sort's 12 bytes of
+ * scratch per element.  This entry point calls no cudaMalloc, cudaFree,
+ * stream-ordered allocator or allocator hook.  Its scratch is one fixed device
+ * array inside this library, sized for GNS_NOALLOC_MAX_N elements (about
+ * 12 MiB); every GPU that loads the library holds that array until the
+ * process exits.  It runs the same passes as gns_sort at buffer_fraction 1.
  *
  * Arguments as gns_sort for float64 keys (device keys, device payload or NULL,
  * n, order); the result is the same stable sort, bit for bit.
  * Errors: GNS_ERR_UNSUPPORTED when n > GNS_NOALLOC_MAX_N (use gns_sort),
- * GNS_ERR_INVALID for bad arguments, GNS_ERR_CUDA if a launch fails.
+ * GNS_ERR_INVALID for bad arguments (as gns_sort, including overlapping keys
+ * and payload), GNS_ERR_CUDA if a launch fails.
  *
  * Set-up: the first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current) and caches it; make that
- * first call before any stream capture that might include later calls.
+ * first call before any stream capture.
  * Sharing: every call on a device uses the same array and the array keeps the
  * last call's contents (the call resets what must start at zero).  Calls that
  * overlap on the GPU -- on different streams, or from different host threads
@@ -227,6 +229,17 @@ void gns_segmented_release(gns_stream_t stream);
  *      that came out larger than `overfull_factor` times the mean is simply
  *      sorted by more merge levels of the same merge path (the plain merge
  *      path is the fallback for it).
+ *   4. check and fallback: after the bucket sort every bucket is sorted, so its
+ *      first and last keys are its minimum and maximum; the check requires the
+ *      bucket offsets to partition [0, n) and, at every bucket boundary, the
+ *      maximum before it to lie strictly below the minimum after it.  Where
+ *      the check fails, the plain
+ *      merge sort (gns_sort at the 100% tier) re-sorts the whole array; the
+ *      decision is taken on the device (the plain sort's kernels return at
+ *      once when the check passes), so the call never waits for the host and
+ *      never returns a wrong order, with or without a report.  Equal keys
+ *      always share a bucket, so they are still in input order when the plain
+ *      sort starts, and its result is the stable sort of the input.
  * buffer_fraction:
  *   >= 1.0      the three phases on the whole array; scratch ~ 16 n bytes for
  *               the partition, then ~ 12 n for the bucket sort (n >= 2^20).
@@ -263,6 +276,8 @@ typedef struct {
                                 they are (already the stable order)           */
     float final_loss;        /* training loss of the last step                 */
     float fit_ms, partition_ms, bucket_sort_ms;   /* per-phase device time     */
+    int verify_failed;       /* 1: the bucket check failed and the plain
+                                merge sort re-sorted the whole array          */
 } gns_learned_report;
 
 int gns_learned_sort(double* keys, uint32_t* payload, int64_t n, int order, double buffer_fraction,
@@ -286,6 +301,29 @@ int gns_mlp_loss_grad(const float* params, const float* x, const float* t, int64
                       float* loss, gns_stream_t stream);
 int gns_mlp_train(const float* x, const float* t, int64_t m, const float* params_in, float* params_out,
                   float* loss_out, int steps, int batch, float learning_rate, gns_stream_t stream);
+
+/* Test hook: plants one fault into the next gns_learned_sort call (consumed
+ * by it) to exercise the bucket check and the plain-sort fallback.  The sort
+ * must still return the exact stable sort.
+ *   GNS_FAULT_BUCKETS_SWAPPED   the partition puts every key of bucket 2k into
+ *                               bucket 2k+1 and the other way round (still a
+ *                               function of the key, so equal keys stay
+ *                               together, but no longer monotone): the bucket
+ *                               check fails and the plain merge sort runs;
+ *   GNS_FAULT_GARBAGE_WEIGHTS   the network weights are overwritten with NaN
+ *                               and +-1e30 before the splitters are derived
+ *                               (useless but ordered splitters: overfull
+ *                               buckets, sorted by more merge levels);
+ *   GNS_FAULT_SPLITTERS_REVERSED the splitter array is reversed before the
+ *                               partition.  A key's bucket comes from binary
+ *                               searches, whose outcome never decreases with
+ *                               the key for any array searched, so the
+ *                               partition stays in order and no fallback is
+ *                               needed.
+ * Any other value clears a pending fault. */
+enum { GNS_FAULT_NONE = 0, GNS_FAULT_BUCKETS_SWAPPED = 1, GNS_FAULT_GARBAGE_WEIGHTS = 2,
+       GNS_FAULT_SPLITTERS_REVERSED = 3 };
+void gns_debug_learned_fault(int kind);
 
 /* Test hook: checks on the host the tree that gns_sort at this buffer_fraction
  * in (0, 1) would run on for n keys (n > 8192): Frogsort1 at [0.5, 1), Frogsort2

@@ -70,6 +70,7 @@ def lib() -> ctypes.CDLL:
                 "gns_set_wait_limit_ns": ([u64], None),
                 "gns_debug_skip_publish": ([i64], None),
                 "gns_learned_half_plan_ok": ([i64], i32),
+                "gns_debug_learned_fault": ([i32], None),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -169,7 +170,8 @@ class LearnedReport(ctypes.Structure):
     _fields_ = [("fallback", ctypes.c_int), ("nonempty_buckets", ctypes.c_int), ("max_bucket", ctypes.c_int64),
                 ("overfull_buckets", ctypes.c_int), ("tied_buckets", ctypes.c_int), ("final_loss", ctypes.c_float),
                 ("fit_ms", ctypes.c_float),
-                ("partition_ms", ctypes.c_float), ("bucket_sort_ms", ctypes.c_float)]
+                ("partition_ms", ctypes.c_float), ("bucket_sort_ms", ctypes.c_float),
+                ("verify_failed", ctypes.c_int)]
 
 
 def gns_learned_sort(keys, payload=None, order: int = ASCENDING, buffer_fraction: float = 1.0,
@@ -298,3 +300,11 @@ def gns_set_wait_limit_ns(ns: int) -> None:
 
 def gns_debug_skip_publish(ticket: int) -> None:
     lib().gns_debug_skip_publish(int(ticket))
+
+
+FAULT_NONE, FAULT_BUCKETS_SWAPPED, FAULT_GARBAGE_WEIGHTS, FAULT_SPLITTERS_REVERSED = 0, 1, 2, 3
+
+
+def gns_debug_learned_fault(kind: int) -> None:
+    """Plant one fault into the next gns_learned_sort call (test hook)."""
+    lib().gns_debug_learned_fault(int(kind))

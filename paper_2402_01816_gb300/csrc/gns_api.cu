@@ -198,16 +198,24 @@ const char* kernel_names[K_COUNT] = {
     "learn_fit", "learn_split", "learn_hist", "learn_scan", "learn_scatter", "learn_verify", "mlp_forward",
     "mlp_backward", "mlp_adam", "noalloc_sort", "learn_half_move"};
 
-}  // namespace gns
+int num_sms()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && cached[dev]) return cached[dev];
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (v <= 0) v = 152;
+    if (dev >= 0 && dev < 64) cached[dev] = v;
+    return v;
+}
 
-using namespace gns;
+namespace {
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+}  // namespace
 
-// ============================================================== C ABI
-extern "C" {
-
-static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
-
-static int check_sort_args(const void* keys, const uint32_t* payload, int64_t n, int order, double bf)
+int check_sort_args(const void* keys, const uint32_t* payload, int64_t n, int order, double bf)
 {
     if (n < 0) return GNS_ERR_INVALID;
     if (order != GNS_ASCENDING && order != GNS_DESCENDING) return GNS_ERR_INVALID;
@@ -225,6 +233,13 @@ static int check_sort_args(const void* keys, const uint32_t* payload, int64_t n,
     if (bf < 1.0 / 64) return GNS_ERR_UNSUPPORTED;   // below Frogsort2's smallest inner fraction
     return GNS_OK;
 }
+
+}  // namespace gns
+
+using namespace gns;
+
+// ============================================================== C ABI
+extern "C" {
 
 static int mode_of(int key_type, int order)
 {

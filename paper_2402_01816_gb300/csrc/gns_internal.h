@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <mutex>
 
 #include "../../include/gns.h"
 
@@ -85,9 +86,47 @@ int finish_call(int rc, cudaStream_t s);
 // Rounds a byte count up to 256 (every workspace sub-buffer starts aligned).
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Runs f() once for each device ordinal it is called on (with that device
+// current): function attributes such as the dynamic shared-memory limit belong
+// to the context of the device that was current when they were set.
+struct PerDeviceOnce {
+    std::mutex mu;
+    bool done[64] = {};
+    template <typename F>
+    void run(F f)
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return;
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev >= 0 && dev < 64 && done[dev]) return;
+        f();
+        if (dev >= 0 && dev < 64) done[dev] = true;
+    }
+};
+
+// Host-side argument checks shared by the sorting entry points: n >= 0, a
+// known order, a non-negative buffer fraction, non-NULL aligned keys when
+// n > 0, an aligned payload that does not overlap the keys.
+int check_sort_args(const void* keys, const uint32_t* payload, int64_t n, int order, double bf);
+
+// Number of SMs of the current device (cached per device).
+int num_sms();
+
 // gns_sort core: keys are raw 64-bit patterns, mode = key type | order bits.
 int sort_device(uint64_t* keys, uint32_t* payload, int64_t n, int mode,
                 double buffer_fraction, cudaStream_t s);
+
+// The 100% tier (tile sort, then Nocopy merge levels) on scratch the caller
+// provides: bufk / bufv hold n keys / n payloads (bufv unused without a
+// payload), splits holds plain_sort_splits(n) int64 words, ctl 256 bytes of
+// control words (reset by the call).  gate == nullptr: a run-detection pass
+// comes first (presorted input costs one read, strictly descending input one
+// reversal).  gate != nullptr: a device int read when the sort starts; every
+// kernel of the sort returns at once unless it is non-zero, so that whether the
+// sort runs is decided on the device.  Returns GNS_OK or GNS_ERR_CUDA.
+int plain_sort_ext(uint64_t* keys, uint32_t* vals, int64_t n, int mode, uint64_t* bufk, uint32_t* bufv,
+                   int64_t* splits, int* ctl, const int* gate, cudaStream_t s);
+int64_t plain_sort_splits(int64_t n);
 size_t sort_workspace_bytes(int64_t n, double buffer_fraction);
 
 // Segmented sort core and helpers (gns_segmented.cu).

@@ -257,6 +257,15 @@ static __global__ void reverse_kernel(uint64_t* keys, uint32_t* vals, int64_t n,
     }
 }
 
+// A sort whose start is decided on the device: with *gate == 0 the presorted
+// flag is raised (every later kernel of the sort returns at once), otherwise
+// both flags are cleared (no run detection: the sort runs in full).
+static __global__ void gate_kernel(const int* gate, int* presorted)
+{
+    presorted[0] = (*gate == 0) ? 1 : 0;
+    presorted[1] = 0;
+}
+
 // ctl[0..1]: presorted flags (nothing left to do), ctl[2]: the call's error
 // word.  Every kernel after run detection returns at once when any is set, so
 // that after a device-side error (a wait that ran out) no later pass runs on

@@ -25,6 +25,9 @@ namespace gns {
 
 namespace {
 
+// Fault planted into the next learned sort (gns_debug_learned_fault; 0 = none).
+std::atomic<int> g_learn_fault{0};
+
 // ---------------------------------------------------------------- the network
 constexpr int MH = 32;                              // hidden units per layer
 constexpr int NP = MH + MH + MH * MH + MH + MH + 1; // 1153 parameters
@@ -281,6 +284,7 @@ struct LearnMeta {
     int bad;              // splitters not non-decreasing (never expected)
     int64_t max_bucket;
     int nonempty, overfull, tied;
+    int verify_failed;    // the bucket check failed: the plain sort re-sorts the array
     uint64_t knot[NKNOTS + 1];   // prefixes of the sample quantiles i/64
 };
 
@@ -342,6 +346,7 @@ __global__ void fit_meta_kernel(const uint64_t* __restrict__ sample, int mode, L
         while ((range >> sh) >= (1ull << TABLE_BITS)) ++sh;
         meta->sh = sh;
         meta->bad = 0;
+        meta->verify_failed = 0;
     }
 }
 
@@ -496,7 +501,7 @@ __global__ void __launch_bounds__(HIST_THREADS)
     part_hist_a_kernel(const uint64_t* __restrict__ keys, int64_t n, int mode, const uint16_t* __restrict__ table,
                        const uint64_t* __restrict__ spl, const LearnMeta* __restrict__ meta,
                        uint16_t* __restrict__ bid, uint32_t* __restrict__ counts, int64_t ntiles,
-                       unsigned long long* btot)
+                       unsigned long long* btot, int bucket_xor)
 {
     __shared__ uint64_t s_spl[NSPLIT];
     __shared__ uint32_t bcnt[NBUCKETS];
@@ -520,7 +525,8 @@ __global__ void __launch_bounds__(HIST_THREADS)
         for (int r = 0; r < PART_TILE / HIST_THREADS; ++r) {
             const int64_t i = base + threadIdx.x + r * HIST_THREADS;
             if (i < n) {
-                const int bk = bucket_of(s_spl, table, raw[r], mode, lo53, range, sh);
+                // bucket_xor is 0 except under the test hook that swaps bucket pairs
+                const int bk = bucket_of(s_spl, table, raw[r], mode, lo53, range, sh) ^ bucket_xor;
                 bid[i] = (uint16_t)bk;
                 atomicAdd(&wcnt[w][bk & 63], 1u);
                 atomicAdd(&bcnt[bk], 1u);
@@ -844,6 +850,53 @@ __global__ void __launch_bounds__(256) tied_final_kernel(const int64_t* __restri
     if (t) atomicAdd(&meta->tied, 1);
 }
 
+// Bucket check (after the bucket sort).  Every bucket is sorted now, so its
+// first key is its smallest and its last key its largest (order-mapped).  The
+// array is the stable sort when the offsets partition [0, n) and, at every
+// bucket boundary p (0 < p < n), the largest key of the buckets before p lies
+// strictly below the smallest key of the buckets from p on: keys of different
+// buckets differ in their 53-bit prefix, so equality across a boundary is a
+// failure as well.  A violation raises meta->verify_failed, which gates the
+// plain sort that follows.  (Splitters out of order, meta->bad, cannot cause
+// one: the bucket function is monotone for any splitter array.)
+__global__ void __launch_bounds__(256) bucket_verify_kernel(const uint64_t* __restrict__ keys,
+                                                            const int64_t* __restrict__ off, int64_t n, int mode,
+                                                            LearnMeta* meta)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    bool fail = false;
+    if (b <= NBUCKETS) {
+        const int64_t p = off[b];
+        if (b == 0) fail = p != 0;
+        else fail = p < off[b - 1];
+        if (b == NBUCKETS) fail |= p != n;
+        else if (b > 0 && p > 0 && p < n) fail |= !(encode_key(keys[p - 1], mode) < encode_key(keys[p], mode));
+    }
+    if (fail) atomicExch(&meta->verify_failed, 1);
+}
+
+// Test hooks (gns_debug_learned_fault): faults planted between the fit and
+// the bucket check, each of which the sort must survive with an exact result.
+// Splitters in reverse order: a key's bucket comes from binary searches, whose
+// outcome never decreases as the key grows, whatever the array searched; so
+// the bucket function stays monotone and the partition stays in order.
+__global__ void fault_reverse_splitters_kernel(uint64_t* spl)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < NSPLIT / 2) {
+        const uint64_t a = spl[j], b = spl[NSPLIT - 1 - j];
+        spl[j] = b;
+        spl[NSPLIT - 1 - j] = a;
+    }
+}
+
+// Garbage network weights: NaN and +-1e30 in turn.
+__global__ void fault_garbage_params_kernel(float* p)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < NP) p[i] = (i % 3 == 0) ? __int_as_float(0x7fc00000) : ((i % 3 == 1) ? 1e30f : -1e30f);
+}
+
 // ---------------------------------------------------------------- host helpers
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 int64_t imin_h(int64_t a, int64_t b) { return a < b ? a : b; }
@@ -856,10 +909,10 @@ int sms_now()
     return v > 0 ? v : 152;
 }
 
-std::once_flag g_learn_attr_once;
+PerDeviceOnce g_learn_attr_once;
 void learn_init_attributes()
 {
-    std::call_once(g_learn_attr_once, [] {
+    g_learn_attr_once.run([] {
         cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FitSmem));
     });
 }
@@ -890,7 +943,7 @@ void init_params_host(float* p)
 // rest until the end of the call.
 struct LearnLayout {
     size_t bufk, bufv, bidA, bidB, counts, big;
-    size_t sample, x, t, params, F, spl, spl_raw, table, meta, rowtot, btot, diff, tied, off, loss, total;
+    size_t sample, x, t, params, F, spl, spl_raw, table, meta, rowtot, btot, diff, tied, off, loss, ctl, total;
     int64_t ntiles;
 };
 
@@ -921,6 +974,7 @@ LearnLayout learn_layout(int64_t n, bool with_vals)
     o.tied = off; off += align256((size_t)NBUCKETS);
     o.off = off; off += align256((size_t)(NBUCKETS + 1) * 8);
     o.loss = off; off += 256;
+    o.ctl = off; off += 256;
     o.total = off;
     return o;
 }
@@ -941,7 +995,7 @@ struct LearnScratch {
 // and sort 2^16 keys, fit the network, and derive the splitters and the
 // key -> bucket-range table (LearnLayout's spl, table and meta).
 int learn_fit_phase(const uint64_t* keys, int64_t n, int mode, const gns_learned_params& prm, char* ws,
-                    const LearnLayout& lay, cudaStream_t s)
+                    const LearnLayout& lay, cudaStream_t s, int fault)
 {
     uint64_t* sample = (uint64_t*)(ws + lay.sample);
     float* x = (float*)(ws + lay.x);
@@ -980,14 +1034,21 @@ int learn_fit_phase(const uint64_t* keys, int64_t n, int mode, const gns_learned
                     prm.train_steps, prm.batch, prm.learning_rate));
         trained = params1;
     }
+    if (fault == GNS_FAULT_GARBAGE_WEIGHTS) {
+        FTRY(launch(K_LEARN_SPLIT, fault_garbage_params_kernel, dim3(cdiv(NP, 256)), dim3(256), 0, s,
+                    (float*)trained));
+    }
     // 2. splitters and the key -> bucket-range table
     FTRY(launch(K_LEARN_SPLIT, grid_eval_kernel, dim3(256), dim3(256), 0, s,
-                prm.train_steps > 0 ? trained : (const float*)nullptr, F));
+                (prm.train_steps > 0 || fault == GNS_FAULT_GARBAGE_WEIGHTS) ? trained : (const float*)nullptr, F));
     FTRY(launch(K_LEARN_SPLIT, running_max_kernel, dim3(1), dim3(1024), 0, s, F));
     FTRY(launch(K_LEARN_SPLIT, splitter_kernel, dim3(cdiv(NSPLIT, 256)), dim3(256), 0, s, (const float*)F, meta,
                 spl_raw));
     FTRY(launch(K_LEARN_SPLIT, isolate_masses_kernel, dim3(cdiv(NSPLIT, 256)), dim3(256), 0, s,
                 (const uint64_t*)spl_raw, spl, meta));
+    if (fault == GNS_FAULT_SPLITTERS_REVERSED) {
+        FTRY(launch(K_LEARN_SPLIT, fault_reverse_splitters_kernel, dim3(cdiv(NSPLIT, 256)), dim3(256), 0, s, spl));
+    }
     FTRY(launch(K_LEARN_SPLIT, table_kernel, dim3((unsigned)(sms * 4)), dim3(256), 0, s, (const uint64_t*)spl,
                 (const LearnMeta*)meta, table));
 #undef FTRY
@@ -1002,7 +1063,7 @@ int learn_fit_phase(const uint64_t* keys, int64_t n, int mode, const gns_learned
 // uses instead of fitting its own (nullptr: fit here).
 int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, const gns_learned_params& prm,
                         gns_learned_report* rep, cudaStream_t s, const LearnScratch* xs = nullptr,
-                        const char* fitted = nullptr)
+                        const char* fitted = nullptr, int fault = 0)
 {
     learn_init_attributes();
     const LearnLayout lay = learn_layout(n, vals != nullptr);
@@ -1051,7 +1112,7 @@ int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, con
         LTRY(cudaMemcpyAsync(meta, fitted + lay.meta, sizeof(LearnMeta), cudaMemcpyDeviceToDevice, s));
         LTRY(cudaMemcpyAsync(loss, fitted + lay.loss, sizeof(float), cudaMemcpyDeviceToDevice, s));
     } else {
-        rc = learn_fit_phase((const uint64_t*)keys, n, mode, prm, ws, lay, s);
+        rc = learn_fit_phase((const uint64_t*)keys, n, mode, prm, ws, lay, s, fault);
         if (rc != GNS_OK) goto done;
     }
     if (rep) LTRY(cudaEventRecord(ev[1], s));
@@ -1062,7 +1123,8 @@ int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, con
         const int64_t hgrid = imin_h(ntiles, (int64_t)sms * 4);
         LTRY(launch(K_LEARN_HIST, part_hist_a_kernel, dim3((unsigned)hgrid), dim3(HIST_THREADS), 0, s,
                     (const uint64_t*)keys, n, mode, (const uint16_t*)table, (const uint64_t*)spl,
-                    (const LearnMeta*)meta, bidA, counts, ntiles, btot));
+                    (const LearnMeta*)meta, bidA, counts, ntiles, btot,
+                    fault == GNS_FAULT_BUCKETS_SWAPPED ? 1 : 0));
         LTRY(launch(K_LEARN_SCAN, row_scan_kernel, dim3(64), dim3(1024), 0, s, counts, ntiles, rowtot));
         const int64_t sgrid = imin_h(ntiles, (int64_t)sms * 3);   // all CTAs resident
         LTRY(launch(K_LEARN_SCATTER, part_scatter_kernel, dim3((unsigned)sgrid), dim3(PART_THREADS), 0, s,
@@ -1090,6 +1152,39 @@ int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, con
     rc = segmented_sort_direct(keys, vals, boff, NBUCKETS, n, mode, (const uint8_t*)tied, s, xs ? xs->bufk : nullptr,
                                xs ? xs->bufv : nullptr);
     if (rc != GNS_OK) goto done;
+    // 4. bucket check; where it fails, the plain merge sort re-sorts the whole
+    // array (decided on the device: with the check passed its kernels return
+    // at once).  Equal keys always share a bucket, so they are still in input
+    // order here, and the plain stable sort of this array is the stable sort of
+    // the input.
+    LTRY(launch(K_LEARN_VERIFY, bucket_verify_kernel, dim3(NBUCKETS / 256 + 1), dim3(256), 0, s,
+                (const uint64_t*)keys, (const int64_t*)boff, n, mode, meta));
+    {
+        char* fb = nullptr;
+        uint64_t* fbk = nullptr;
+        uint32_t* fbv = nullptr;
+        int64_t* fsplits = nullptr;
+        if (xs) {
+            // the leaf's carved scratch is free again: buffers, and the bucket
+            // ids' 2 n bytes hold the n / CHUNK splits
+            fbk = xs->bufk;
+            fbv = xs->bufv;
+            fsplits = (int64_t*)xs->bidA;
+        } else {
+            const size_t kb = align256((size_t)n * 8), vb = vals ? align256((size_t)n * 4) : 0;
+            fb = (char*)ws_alloc(kb + vb + align256((size_t)plain_sort_splits(n) * 8), s);
+            if (!fb) {
+                rc = GNS_ERR_OOM;
+                goto done;
+            }
+            fbk = (uint64_t*)fb;
+            fbv = vals ? (uint32_t*)(fb + kb) : nullptr;
+            fsplits = (int64_t*)(fb + kb + vb);
+        }
+        rc = plain_sort_ext(keys, vals, n, mode, fbk, fbv, fsplits, (int*)(ws + lay.ctl), &meta->verify_failed, s);
+        if (fb) ws_free(fb, s);
+        if (rc != GNS_OK) goto done;
+    }
     if (rep) {
         LTRY(cudaEventRecord(ev[3], s));
         LearnMeta hm;
@@ -1106,7 +1201,7 @@ int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, con
         cudaEventElapsedTime(&rep->fit_ms, ev[0], ev[1]);
         cudaEventElapsedTime(&rep->partition_ms, ev[1], ev[2]);
         cudaEventElapsedTime(&rep->bucket_sort_ms, ev[2], ev[3]);
-        if (hm.bad) rc = GNS_ERR_INTERNAL;
+        rep->verify_failed = hm.verify_failed;
     }
 #undef LTRY
 done:
@@ -1276,7 +1371,7 @@ __global__ void __launch_bounds__(256) half_move_kernel(Slots sl, int64_t src, i
 // The learned sort within about half a buffer (all checks done by the caller).
 // GNS_ERR_UNSUPPORTED (nothing launched): the memory plan does not fit.
 int learned_half_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, const gns_learned_params& prm,
-                             gns_learned_report* rep, cudaStream_t s)
+                             gns_learned_report* rep, cudaStream_t s, int fault)
 {
     HalfPlan P;
     if (!half_plan(n, vals != nullptr, P)) return GNS_ERR_UNSUPPORTED;
@@ -1316,7 +1411,7 @@ int learned_half_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode
     } while (0)
     HTRY(cudaMemsetAsync(ctl, 0, 256, s));
     if (rep) HTRY(cudaEventRecord(fev[0], s));
-    rc = learn_fit_phase(keys, n, mode, prm, fitws, flay, s);
+    rc = learn_fit_phase(keys, n, mode, prm, fitws, flay, s, fault);
     if (rc != GNS_OK) goto done;
     if (rep) {
         HTRY(cudaEventRecord(fev[1], s));
@@ -1332,8 +1427,9 @@ int learned_half_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode
         xs.bidB = (uint16_t*)at(L.bidB);
         xs.counts = (uint32_t*)at(L.counts);
         gns_learned_report lr;
+        // the leaves reuse the shared fit; a planted partition fault reaches them
         rc = learned_sort_device(keys + L.src, vals ? vals + L.src : nullptr, L.m, mode, prm, rep ? &lr : nullptr, s,
-                                 &xs, fitws);
+                                 &xs, fitws, fault == GNS_FAULT_BUCKETS_SWAPPED ? fault : 0);
         if (rc != GNS_OK) goto done;
         if (rep) {
             rep->nonempty_buckets += lr.nonempty_buckets;
@@ -1344,6 +1440,7 @@ int learned_half_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode
             rep->fit_ms += lr.fit_ms;
             rep->partition_ms += lr.partition_ms;
             rep->bucket_sort_ms += lr.bucket_sort_ms;
+            rep->verify_failed |= lr.verify_failed;
         }
         HTRY(launch(K_LEARN_HALF, half_move_kernel, dim3((unsigned)imin_h(cdiv(L.m, 256), (int64_t)sms_now() * 8)),
                     dim3(256), 0, s, sl, L.src, L.dst, L.m, mode));
@@ -1387,6 +1484,11 @@ size_t learned_workspace_bytes(int64_t n, double bf)
 using namespace gns;
 
 extern "C" {
+
+void gns_debug_learned_fault(int kind)
+{
+    g_learn_fault.store(kind >= GNS_FAULT_BUCKETS_SWAPPED && kind <= GNS_FAULT_SPLITTERS_REVERSED ? kind : 0);
+}
 
 int gns_learned_half_plan_ok(int64_t n)
 {
@@ -1441,19 +1543,20 @@ int gns_learned_sort(double* keys, uint32_t* payload, int64_t n, int order, doub
     if (prm.train_steps < 0 || prm.batch <= 0 || prm.batch % 512 != 0 || !(prm.learning_rate > 0.f) ||
         !(prm.overfull_factor > 0.f))
         return GNS_ERR_INVALID;
-    if (n < 0 || (order != GNS_ASCENDING && order != GNS_DESCENDING) || isnan(buffer_fraction) ||
-        buffer_fraction < 0.0)
-        return GNS_ERR_INVALID;
-    if (n > 0 && !keys) return GNS_ERR_INVALID;
-    if (((uintptr_t)keys & 7) || ((uintptr_t)payload & 3)) return GNS_ERR_INVALID;
+    {
+        // the same host checks as gns_sort (overlap of keys and payload included)
+        const int ac = check_sort_args(keys, payload, n, order, buffer_fraction);
+        if (ac == GNS_ERR_INVALID) return ac;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     if (report) memset(report, 0, sizeof(*report));
     const int mode = order == GNS_DESCENDING ? MODE_DESC : 0;
+    const int fault = g_learn_fault.exchange(0);
     int rc = GNS_ERR_UNSUPPORTED;
     if (buffer_fraction >= 1.0 && n >= (1ll << 20))
-        rc = learned_sort_device((uint64_t*)keys, payload, n, mode, prm, report, s);
+        rc = learned_sort_device((uint64_t*)keys, payload, n, mode, prm, report, s, nullptr, nullptr, fault);
     else if (buffer_fraction >= 0.5 && n >= HALF_MIN_N)
-        rc = learned_half_sort_device((uint64_t*)keys, payload, n, mode, prm, report, s);
+        rc = learned_half_sort_device((uint64_t*)keys, payload, n, mode, prm, report, s, fault);
     if (rc == GNS_ERR_UNSUPPORTED) {
         // too few keys to pay for the fit, a buffer below one half, or no room
         // for a leaf's scratch: the plain sort at this buffer fraction

@@ -313,10 +313,10 @@ SegLayout seg_layout(int64_t n, int64_t nseg, bool with_vals, bool ext_buf = fal
     return o;
 }
 
-std::once_flag g_seg_attr_once;
+PerDeviceOnce g_seg_attr_once;
 void seg_init_attributes()
 {
-    std::call_once(g_seg_attr_once, [] {
+    g_seg_attr_once.run([] {
         cudaFuncSetAttribute(seg_tile_kernel<256, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(SmemKV<4096>));
         cudaFuncSetAttribute(seg_tile_kernel<512, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -36,19 +36,6 @@ constexpr size_t ws_smem() { return sizeof(WsSmem<WS_CHUNK, S>); }
 template <int S>
 constexpr size_t ws_smem_out() { return sizeof(WsSmemOut<WS_CHUNK, S>); }
 
-int num_sms()
-{
-    static int cached[64] = {0};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 64 && cached[dev]) return cached[dev];
-    int v = 0;
-    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    if (v <= 0) v = 152;
-    if (dev < 64) cached[dev] = v;
-    return v;
-}
-
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 int64_t imin(int64_t a, int64_t b) { return a < b ? a : b; }
 
@@ -261,11 +248,11 @@ void set_smem(K kernel, size_t bytes)
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-std::once_flag g_attr_once;
+PerDeviceOnce g_attr_once;
 
 void init_attributes()
 {
-    std::call_once(g_attr_once, [] {
+    g_attr_once.run([] {
         set_smem(tile_sort_kernel<SORT_THREADS, SORT_ITEMS>, kSmemTile);
         set_smem(frog_setup_kernel<SORT_THREADS, SORT_ITEMS>, kSmemTile);
         set_smem(merge_pass_ws_kernel<2>, ws_smem_out<2>());
@@ -321,12 +308,25 @@ int64_t resident_ctas(K kernel, int threads, size_t smem)
     return (int64_t)v * num_sms();
 }
 
+// Resident CTAs of a kernel at its launch shape on the current device, looked
+// up once per device.
+template <typename K>
+int64_t resident_ctas_cached(int64_t (&cache)[64], K kernel, int threads, size_t smem)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return resident_ctas(kernel, threads, smem);
+    if (!cache[dev]) cache[dev] = resident_ctas(kernel, threads, smem);
+    return cache[dev];
+}
+
 template <int S>
 cudaError_t launch_plain_level_ws(const uint64_t* sk, const uint32_t* sv, uint64_t* dk, uint32_t* dv, int64_t n,
                                   int64_t w, int64_t nblocks, const int64_t* splits, int mode, int decode,
                                   int* call_err, uint64_t limit, const int* skip, cudaStream_t s)
 {
-    static const int64_t cap = resident_ctas(merge_pass_ws_kernel<S>, WS_CONSUMERS + 32, ws_smem_out<S>());
+    static int64_t caps[64] = {};
+    const int64_t cap = resident_ctas_cached(caps, merge_pass_ws_kernel<S>, WS_CONSUMERS + 32, ws_smem_out<S>());
     const int64_t grid = imin(nblocks, cap);
     return launch(K_MERGE_PASS, merge_pass_ws_kernel<S>, dim3((unsigned)grid), dim3(WS_CONSUMERS + 32),
                   ws_smem_out<S>(), s, sk, sv, dk, dv, n, w, nblocks, splits, mode, decode, call_err, limit, skip);
@@ -337,7 +337,8 @@ cudaError_t launch_frog_level_ws(const Slots& sl, const FrogItem* items, int64_t
                                  int* ticket, int* loaded, int epoch, int* call_err, uint64_t limit,
                                  int64_t skip_ticket, const int* skip, cudaStream_t s)
 {
-    static const int64_t cap = resident_ctas(frog_merge_ws_kernel<S>, WS_CONSUMERS + 32, ws_smem<S>());
+    static int64_t caps[64] = {};
+    const int64_t cap = resident_ctas_cached(caps, frog_merge_ws_kernel<S>, WS_CONSUMERS + 32, ws_smem<S>());
     const int64_t grid = imin(total, cap);
     return launch(K_FROG_MERGE, frog_merge_ws_kernel<S>, dim3((unsigned)grid), dim3(WS_CONSUMERS + 32), ws_smem<S>(),
                   s, sl, items, total, mode, decode, ticket, loaded, epoch, call_err, limit, skip_ticket, skip);
@@ -402,10 +403,83 @@ size_t sort_workspace_bytes(int64_t n, double bf)
     return make_layout(n, bf, true, nullptr).total;
 }
 
+namespace {
+
+// Run detection (one read pass) and the reversal of strictly descending input;
+// ctl must be reset already.
+cudaError_t detect_and_reverse(uint64_t* keys, uint32_t* vals, int64_t n, int mode, int* ctl, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(ctl, 1, 2 * sizeof(int), s);   // both flags "true"
+    if (e != cudaSuccess) return e;
+    // one wave of persistent CTAs: a second partial wave would start its tiles late
+    static int64_t caps[64] = {};
+    const int64_t detect_cap = resident_ctas_cached(caps, run_detect_kernel, DETECT_THREADS, 0);
+    e = launch(K_RUN_DETECT, run_detect_kernel, dim3((unsigned)imin(ceil_div(n, DETECT_TILE), detect_cap)),
+               dim3(DETECT_THREADS), 0, s, (const uint64_t*)keys, n, mode, ctl);
+    if (e != cudaSuccess) return e;
+    return launch(K_REVERSE, reverse_kernel, dim3((unsigned)(num_sms() * 8)), dim3(256), 0, s, keys, vals, n,
+                  (const int*)ctl);
+}
+
+}  // namespace
+
+int64_t plain_sort_splits(int64_t n) { return n > TILE ? ceil_div(n, CHUNK) : 0; }
+
+int plain_sort_ext(uint64_t* keys, uint32_t* vals, int64_t n, int mode, uint64_t* bufk, uint32_t* bufv,
+                   int64_t* splits, int* ctl, const int* gate, cudaStream_t s)
+{
+    if (n <= 1) return GNS_OK;
+    init_attributes();
+    int rc = GNS_OK;
+    int* call_err = ctl + 2;
+    const int* skip = ctl;
+    const int L = merge_levels(n);
+    uint64_t* cur_k = (L & 1) ? bufk : keys;
+    uint32_t* cur_v = (L & 1) ? bufv : vals;
+    uint64_t* oth_k = (L & 1) ? keys : bufk;
+    uint32_t* oth_v = (L & 1) ? vals : bufv;
+    if (!vals) cur_v = oth_v = nullptr;
+    const int64_t nblocks = ceil_div(n, CHUNK);
+    GNS_TRY(cudaMemsetAsync(ctl, 0, 256, s));
+    if (gate)
+        GNS_TRY(launch(K_RUN_DETECT, gate_kernel, dim3(1), dim3(1), 0, s, gate, ctl));
+    else
+        GNS_TRY(detect_and_reverse(keys, vals, n, mode, ctl, s));
+    // the tile sort writes to the buffer when the level count is odd, so that
+    // the last level lands in the caller's arrays; with no level it decodes
+    GNS_TRY(launch(K_TILE_SORT, tile_sort_kernel<SORT_THREADS, SORT_ITEMS>, dim3((unsigned)ceil_div(n, TILE)),
+                   dim3(SORT_THREADS), kSmemTile, s, (const uint64_t*)keys, (const uint32_t*)vals, cur_k, cur_v, n,
+                   mode, (int)(L == 0), skip));
+    for (int lvl = 0; lvl < L; ++lvl) {
+        const int64_t w = (int64_t)TILE << lvl;
+        GNS_TRY(launch(K_MERGE_PARTITION, merge_partition_kernel, dim3((unsigned)ceil_div(nblocks, 256)), dim3(256),
+                       0, s, (const uint64_t*)cur_k, n, w, nblocks, splits, skip));
+        GNS_TRY(launch_plain_level((const uint64_t*)cur_k, (const uint32_t*)cur_v, oth_k, oth_v, n, w, nblocks,
+                                   (const int64_t*)splits, mode, (int)(lvl == L - 1), call_err, wait_limit_ns(), skip,
+                                   s));
+        uint64_t* tk = cur_k; cur_k = oth_k; oth_k = tk;
+        uint32_t* tv = cur_v; cur_v = oth_v; oth_v = tv;
+    }
+    GNS_TRY(publish_call_error(call_err, s));
+done:
+    return rc;
+}
+
 int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, cudaStream_t s)
 {
     if (n <= 1) return GNS_OK;
-    const bool frog2 = bf < 0.5 && n > TILE;
+    if (bf >= 1.0 || n <= TILE) {
+        const Layout lay = make_layout(n, 1.0, vals != nullptr, nullptr);
+        char* ws = (char*)ws_alloc(lay.total, s);
+        if (!ws) return GNS_ERR_OOM;
+        const int rc = plain_sort_ext(keys, vals, n, mode, n > TILE ? (uint64_t*)(ws + lay.bufk) : nullptr,
+                                      (vals && n > TILE) ? (uint32_t*)(ws + lay.bufv) : nullptr,
+                                      n > TILE ? (int64_t*)(ws + lay.splits) : nullptr, (int*)(ws + lay.ctl),
+                                      nullptr, s);
+        ws_free(ws, s);
+        return rc;
+    }
+    const bool frog2 = bf < 0.5;
     std::unique_lock<std::mutex> plan_lock(g_frog2_mu, std::defer_lock);
     const Frog2Dev* fp = nullptr;
     if (frog2) {
@@ -419,24 +493,13 @@ int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, 
     init_attributes();
     int rc = GNS_OK;
     int* ctl = (int*)(ws + lay.ctl);
-    int* presorted = ctl;
     int* call_err = ctl + 2;
-    const int* skip = presorted;
+    const int* skip = ctl;
 
     GNS_TRY(cudaMemsetAsync(ctl, 0, 256, s));
-    GNS_TRY(cudaMemsetAsync(presorted, 1, 2 * sizeof(int), s));   // both flags "true"
-    {
-        // one wave of persistent CTAs: a second partial wave would start its tiles late
-        static const int64_t detect_cap = resident_ctas(run_detect_kernel, DETECT_THREADS, 0);
-        GNS_TRY(launch(K_RUN_DETECT, run_detect_kernel, dim3((unsigned)imin(ceil_div(n, DETECT_TILE), detect_cap)),
-                       dim3(DETECT_THREADS), 0, s, (const uint64_t*)keys, n, mode, presorted));
-    }
-    GNS_TRY(launch(K_REVERSE, reverse_kernel, dim3(152 * 8), dim3(256), 0, s, keys, vals, n, (const int*)presorted));
+    GNS_TRY(detect_and_reverse(keys, vals, n, mode, ctl, s));
 
-    if (n <= TILE) {
-        GNS_TRY(launch(K_TILE_SORT, tile_sort_kernel<SORT_THREADS, SORT_ITEMS>, dim3(1), dim3(SORT_THREADS),
-                       kSmemTile, s, (const uint64_t*)keys, (const uint32_t*)vals, keys, vals, n, mode, 1, skip));
-    } else if (frog2) {
+    if (frog2) {
         const int D = lay.D;
         Slots sl;
         sl.k0 = keys; sl.v0 = vals; sl.n = n; sl.b = n * frog2_num(bf) / FROG2_DEN;
@@ -473,30 +536,6 @@ int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, 
             GNS_TRY(launch_frog_level(sl, (const FrogItem*)items, total, mode, (int)(d == 0), tickets + d, lflags,
                                       D - d, call_err, limit, skip_ticket, skip, s));
             skip_ticket = -1;
-        }
-    } else if (bf >= 1.0) {
-        const int L = lay.L;
-        uint64_t* bufk = (uint64_t*)(ws + lay.bufk);
-        uint32_t* bufv = vals ? (uint32_t*)(ws + lay.bufv) : nullptr;
-        int64_t* splits = (int64_t*)(ws + lay.splits);
-        uint64_t* cur_k = (L & 1) ? bufk : keys;
-        uint32_t* cur_v = (L & 1) ? bufv : vals;
-        uint64_t* oth_k = (L & 1) ? keys : bufk;
-        uint32_t* oth_v = (L & 1) ? vals : bufv;
-        const int64_t tiles = ceil_div(n, TILE);
-        GNS_TRY(launch(K_TILE_SORT, tile_sort_kernel<SORT_THREADS, SORT_ITEMS>, dim3((unsigned)tiles),
-                       dim3(SORT_THREADS), kSmemTile, s, (const uint64_t*)keys, (const uint32_t*)vals, cur_k,
-                       cur_v, n, mode, 0, skip));
-        const int64_t nblocks = ceil_div(n, CHUNK);
-        for (int lvl = 0; lvl < L; ++lvl) {
-            const int64_t w = (int64_t)TILE << lvl;
-            GNS_TRY(launch(K_MERGE_PARTITION, merge_partition_kernel, dim3((unsigned)ceil_div(nblocks, 256)),
-                           dim3(256), 0, s, (const uint64_t*)cur_k, n, w, nblocks, splits, skip));
-            GNS_TRY(launch_plain_level((const uint64_t*)cur_k, (const uint32_t*)cur_v, oth_k, oth_v, n, w, nblocks,
-                                       (const int64_t*)splits, mode, (int)(lvl == L - 1), call_err, wait_limit_ns(),
-                                       skip, s));
-            uint64_t* tk = cur_k; cur_k = oth_k; oth_k = tk;
-            uint32_t* tv = cur_v; cur_v = oth_v; oth_v = tv;
         }
     } else {
         const int D = lay.D;

@@ -166,3 +166,31 @@ def test_frog_plan_invariants(L, bf):
     for n in sizes:
         assert L.gns_frog_plan_check(n, bf) == 0, (n, bf)
     assert L.gns_frog_plan_check(T, bf) == -1            # one tile: no tree
+
+
+@pytest.mark.parametrize("args,code", [
+    ((FAKE, None, -1, 0), -1),                 # n < 0
+    ((None, None, 10, 0), -1),                 # NULL keys with n > 0
+    ((FAKE, None, 10, 2), -1),                 # unknown order
+    ((FAKE + 4, None, 10, 0), -1),             # keys not 8-byte aligned
+    ((FAKE, FAKE + 2, 10, 0), -1),             # payload misaligned
+    ((FAKE, FAKE + 40, 10, 0), -1),            # keys and payload overlap
+    ((FAKE + 32, FAKE, 10, 0), -1),            # payload overlapping the keys from below
+    ((FAKE, None, (1 << 20) + 1, 0), -2),      # beyond the fixed scratch: use gns_sort
+    ((None, None, 0, 0), 0),                   # n == 0 is a no-op
+    ((FAKE, None, 1, 1), 0),                   # n == 1 is a no-op
+])
+def test_noalloc_host_argument_checks(L, args, code):
+    """gns_sort_noalloc rejects what gns_sort rejects, and sizes beyond its
+    fixed scratch, before any device work."""
+    k, p, n, order = args
+    assert L.gns_sort_noalloc(k, p, n, order, None) == code
+
+
+@pytest.mark.parametrize("args", [
+    (FAKE, None, -1, 0, 1.0), (None, None, 10, 0, 1.0), (FAKE, None, 10, 2, 1.0),
+    (FAKE, None, 10, 0, math.nan), (FAKE + 4, None, 10, 0, 1.0), (FAKE, FAKE + 40, 10, 0, 1.0),
+])
+def test_learned_host_argument_checks(L, args):
+    k, p, n, order, bf = args
+    assert L.gns_learned_sort(k, p, n, order, bf, None, None, None) == -1

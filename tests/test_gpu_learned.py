@@ -156,6 +156,69 @@ N_HALF = (1 << 22) + 12347     # four leaves of about 2^20 keys, ragged
 
 
 @pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("bf", [1.0, 0.5])
+def test_misordered_partition_falls_back_to_plain_sort(bf, order):
+    """A partition planted out of order (every key of bucket 2k sent to bucket
+    2k+1 and the other way round): the bucket check fails, the plain merge sort
+    re-sorts the whole array on the device, and the result is still exactly
+    the oracle's stable sort -- with a report (which says so) and without one
+    (no status error, no wrong order)."""
+    need_gpu()
+    import paper_2402_01816_gb300 as g
+    n = N if bf == 1.0 else N_HALF
+    keys = inputs.make_keys("mixture", n, seed=31)
+    g.gns_debug_learned_fault(g.FAULT_BUCKETS_SWAPPED)
+    rep = _learned(keys, order=order, buffer_fraction=bf)
+    assert rep["verify_failed"] == 1 and rep["fallback"] == 0, rep
+    # no report requested: the same fallback, decided on the device
+    g.gns_debug_learned_fault(g.FAULT_BUCKETS_SWAPPED)
+    pay = inputs.index_payload(n)
+    kt, pt = to_dev_keys(keys), to_dev_payload(pay)
+    g.gns_learned_sort(kt, pt, order=order, buffer_fraction=bf)
+    assert g.gns_stream_status() == 0
+    want_k, want_p = oracle.stable_sort(keys, pay, oracle.DESC if order else oracle.ASC)
+    assert_bitexact(kt.cpu().numpy(), pt.cpu().numpy().view(np.uint32), want_k, want_p)
+    # the fault is consumed: the next call is clean
+    assert _learned(keys, order=order, buffer_fraction=bf)["verify_failed"] == 0
+
+
+def test_reversed_splitters_keep_the_partition_in_order():
+    """Splitters reversed before the partition: a key's bucket comes from
+    binary searches, whose outcome never decreases as the key grows whatever
+    array is searched, so the buckets stay in order, the check passes and the
+    result is exact without the fallback."""
+    need_gpu()
+    import paper_2402_01816_gb300 as g
+    keys = inputs.make_keys("mixture", N, seed=34)
+    g.gns_debug_learned_fault(g.FAULT_SPLITTERS_REVERSED)
+    rep = _learned(keys)
+    assert rep["verify_failed"] == 0, rep
+
+
+def test_garbage_network_weights_stay_exact():
+    """NaN and +-1e30 weights make every splitter the same: one bucket takes
+    nearly every key and is sorted by more merge levels of the same merge
+    path.  The check passes (the splitters are in order) and the result is
+    exact."""
+    need_gpu()
+    import paper_2402_01816_gb300 as g
+    keys = inputs.make_keys("mixture", N, seed=32)
+    g.gns_debug_learned_fault(g.FAULT_GARBAGE_WEIGHTS)
+    rep = _learned(keys)
+    assert rep["verify_failed"] == 0 and rep["max_bucket"] > N // 2 and rep["overfull_buckets"] >= 1, rep
+    g.gns_debug_learned_fault(g.FAULT_GARBAGE_WEIGHTS)
+    assert _learned(keys, order=1, train_steps=0)["max_bucket"] > N // 2     # without training, too
+
+
+def test_tiny_overfull_cap_stays_exact():
+    """An overfull cap far below the mean bucket: every bucket counts as
+    overfull and takes the merge path; the result is exact."""
+    need_gpu()
+    rep = _learned(inputs.make_keys("mixture", N, seed=33), overfull_factor=1e-3)
+    assert rep["overfull_buckets"] == rep["nonempty_buckets"] > 1, rep
+
+
+@pytest.mark.parametrize("order", [0, 1])
 @pytest.mark.parametrize("pattern", ["mixture", "ties", "permut", "asc_noise", "desc"])
 def test_learned_half_buffer_exact(pattern, order):
     """The half-buffer form (four learned-sorted leaves of a two-level
