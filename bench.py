@@ -357,7 +357,8 @@ def paper_patterns(dev, n=1 << 27):
     out = {"workload": f"paper patterns, {n} float64 keys + uint32 index payload, 100% and 50% buffer",
            "patterns": {}}
     pay = torch.arange(n, dtype=torch.int64, device=dev).to(torch.int32)
-    tot = {1.0: 0.0, 0.5: 0.0}
+    tot = {1.0: 0.0, 0.5: 0.0, "squid": 0.0}
+    total5 = inputs.PAPER_PATTERNS[:5]       # the TOTAL KPI: permut, tielog2, ascall, asclocal, ascglobal
     for pattern in inputs.PAPER_PATTERNS:
         keys = torch.from_numpy(inputs.make_keys(pattern, n, seed=0)).to(dev)
         kt, pt = torch.empty_like(keys), torch.empty_like(pay)
@@ -372,7 +373,14 @@ def paper_patterns(dev, n=1 << 27):
             t = _time_ms(lambda: g.gns_sort(kt, pt, buffer_fraction=bf), restore)
             ram = 1.0 + g.gns_workspace_bytes(n, bf) / (12.0 * n)
             row[f"{int(bf * 100)}%"] = {"ms": t, "gkeys_s": n / t / 1e6, "pct_ram": ram, "t_footprint_ms": ram * t}
-            tot[bf] += t
+            if pattern in total5:
+                tot[bf] += t
+        restore()
+        g.gns_sort_symmetric(kt, pt, variant=g.SQUIDSORT1)
+        t = _time_ms(lambda: g.gns_sort_symmetric(kt, pt, variant=g.SQUIDSORT1), restore)
+        row["50%-squidsort1"] = {"ms": t, "gkeys_s": n / t / 1e6, "r_runtime_vs_100": t / row["100%"]["ms"]}
+        if pattern in total5:
+            tot["squid"] += t
         if g.gns_stream_status() != 0:
             raise RuntimeError("device status error in paper_patterns")
         a, b = row["100%"], row["50%"]
@@ -384,7 +392,50 @@ def paper_patterns(dev, n=1 << 27):
         torch.cuda.empty_cache()
     r_ram = (1.0 + g.gns_workspace_bytes(n, 0.5) / (12.0 * n)) / (1.0 + g.gns_workspace_bytes(n, 1.0) / (12.0 * n))
     out["TOTAL"] = {"ms_100": tot[1.0], "ms_50": tot[0.5], "r_pct_ram": r_ram, "r_runtime": tot[0.5] / tot[1.0],
-                    "r_t_footprint": r_ram * tot[0.5] / tot[1.0]}
+                    "r_t_footprint": r_ram * tot[0.5] / tot[1.0],
+                    "patterns": list(total5), "ms_50_squidsort1": tot["squid"],
+                    "r_runtime_squidsort1": tot["squid"] / tot[1.0]}
+    return out
+
+
+SYM_PATTERNS = ("permut", "asc_noise", "desc_noise", "desc_ties", "desc_runs")
+
+
+def symmetric_variants(dev, n=1 << 27, host=None):
+    """gns_sort_symmetric: Frogsort1, Geckosort1 and Squidsort1 on Frogsort1's
+    layout (50% buffer), on random input and on the inputs where the
+    orientation of the runs matters (descending with noise, with ties, and in
+    long runs)."""
+    import torch
+    import paper_2402_01816_gb300 as g
+    from paper_2402_01816_gb300 import inputs
+    names = {g.FROGSORT1: "frogsort1", g.GECKOSORT1: "geckosort1", g.SQUIDSORT1: "squidsort1"}
+    out = {"workload": f"symmetric merging variants at 50% buffer: {n} float64 keys + uint32 index payload",
+           "patterns": {}}
+    pay = torch.arange(n, dtype=torch.int64, device=dev).to(torch.int32)
+    for pattern in SYM_PATTERNS:
+        src = host[pattern] if host and pattern in host else inputs.make_keys(pattern, n, seed=0)
+        keys = torch.from_numpy(src).to(dev)
+        kt, pt = torch.empty_like(keys), torch.empty_like(pay)
+
+        def restore():
+            kt.copy_(keys)
+            pt.copy_(pay)
+        row = {}
+        for v, nm in names.items():
+            restore()
+            g.gns_sort_symmetric(kt, pt, variant=v)
+            t = _time_ms(lambda: g.gns_sort_symmetric(kt, pt, variant=v), restore)
+            row[nm] = {"ms": t, "gkeys_s": n / t / 1e6}
+        restore()
+        row["plain_100pct_ms"] = _time_ms(lambda: g.gns_sort(kt, pt), restore)
+        for nm in ("geckosort1", "squidsort1"):
+            row[f"{nm}_speedup_vs_frogsort1"] = row["frogsort1"]["ms"] / row[nm]["ms"]
+        if g.gns_stream_status() != 0:
+            raise RuntimeError("device status error in symmetric_variants")
+        out["patterns"][pattern] = row
+        del keys, kt, pt
+        torch.cuda.empty_cache()
     return out
 
 
@@ -577,6 +628,7 @@ def run_ours(args, ws, rank, local):
     if not args.no_extras and args.n == N_FULL:
         extras["learned_vs_plain"] = learned_vs_plain(dev)
         extras["batched_vs_plain"] = batched_vs_plain(dev)
+        extras["symmetric_variants"] = symmetric_variants(dev, n, host)
     if args.paper_patterns:
         extras["paper_patterns"] = paper_patterns(dev, args.n)
     if args.large:

@@ -20,6 +20,7 @@ GNS_OK, GNS_ERR_INVALID, GNS_ERR_UNSUPPORTED, GNS_ERR_OOM, GNS_ERR_CUDA, GNS_ERR
 GNS_ERR_INTERNAL = -6
 ASCENDING, DESCENDING = 0, 1
 KEY_F64, KEY_I64 = 0, 1
+FROGSORT1, GECKOSORT1, SQUIDSORT1 = 0, 1, 2
 WS_SORT, WS_LEARNED = 0, 1
 
 _lock = threading.Lock()
@@ -46,6 +47,7 @@ def lib() -> ctypes.CDLL:
             sig = {
                 "gns_sort": ([P, P, i64, i32, f64, P], i32),
                 "gns_sort_i64": ([P, P, i64, i32, f64, P], i32),
+                "gns_sort_symmetric": ([P, i32, P, i64, i32, i32, P], i32),
                 "gns_sort_host": ([P, P, i64, i32, i32, f64, P], i32),
                 "gns_sort_noalloc": ([P, P, i64, i32, P], i32),
                 "gns_learned_sort": ([P, P, i64, i32, f64, P, P, P], i32),
@@ -127,6 +129,25 @@ def gns_sort(keys, payload=None, order: int = ASCENDING, buffer_fraction: float 
         raise TypeError("keys must be float64 or int64")
     _check(fn(_dev_ptr(keys, kd, "keys"), _dev_ptr(payload, torch.int32, "payload"), n, order,
               float(buffer_fraction), _stream(stream)), "gns_sort")
+
+
+def gns_sort_symmetric(keys, payload=None, order: int = ASCENDING, variant: int = SQUIDSORT1,
+                       stream=None) -> None:
+    """In-place stable sort on Frogsort1's layout (buffer fraction 1/2) in one
+    of the symmetric variants: FROGSORT1, GECKOSORT1 or SQUIDSORT1."""
+    import torch
+    n = keys.numel()
+    if payload is not None and payload.numel() != n:
+        raise ValueError("payload must have as many elements as keys")
+    if keys.dtype == torch.float64:
+        kt = KEY_F64
+    elif keys.dtype == torch.int64:
+        kt = KEY_I64
+    else:
+        raise TypeError("keys must be float64 or int64")
+    _check(lib().gns_sort_symmetric(_dev_ptr(keys, keys.dtype, "keys"), kt,
+                                    _dev_ptr(payload, torch.int32, "payload"), n, order, int(variant),
+                                    _stream(stream)), "gns_sort_symmetric")
 
 
 def gns_sort_host(keys: np.ndarray, payload: np.ndarray | None = None, order: int = ASCENDING,

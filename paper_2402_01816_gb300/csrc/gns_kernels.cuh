@@ -212,11 +212,9 @@ static __global__ void __launch_bounds__(DETECT_THREADS) run_detect_kernel(const
     }
 }
 
-// Reverses a strictly decreasing array in place (Octosort's final reversal: the
-// reverse of a strictly ordered run is the stable sort, as it has no ties).
-static __global__ void reverse_kernel(uint64_t* keys, uint32_t* vals, int64_t n, const int* presorted)
+// Reverses keys[0, n) and vals[0, n) in place (grid-stride over the CTAs).
+__device__ __forceinline__ void reverse_body(uint64_t* keys, uint32_t* vals, int64_t n)
 {
-    if (presorted[0] != 0 || presorted[1] == 0) return;
     const int64_t half = n / 2;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if (n % 8 == 0 && ((uintptr_t)keys & 15) == 0 && ((uintptr_t)vals & 15) == 0) {
@@ -255,6 +253,14 @@ static __global__ void reverse_kernel(uint64_t* keys, uint32_t* vals, int64_t n,
             vals[i] = y; vals[j] = x;
         }
     }
+}
+
+// Reverses a strictly decreasing array in place (Octosort's final reversal: the
+// reverse of a strictly ordered run is the stable sort, as it has no ties).
+static __global__ void reverse_kernel(uint64_t* keys, uint32_t* vals, int64_t n, const int* presorted)
+{
+    if (presorted[0] != 0 || presorted[1] == 0) return;
+    reverse_body(keys, vals, n);
 }
 
 // A sort whose start is decided on the device: with *gate == 0 the presorted
@@ -345,10 +351,21 @@ static __global__ void merge_partition_kernel(const uint64_t* __restrict__ k, in
 // what the in-place merge needs.
 //
 // Slots [0, n) are the caller's arrays, slots [n, n + floor(n/2)) the buffer.
+//
+// ori is the orientation a node's sorted run is stored in (0 for every node of
+// Frogsort1): 0 = ascending from left to right (the target order itself), 1 =
+// its mirror image, the same sequence stored right to left.  The symmetric
+// variants give nodes either orientation ("Symmetric merging" section:
+// Geckosort sorts data-left branches left-ascending and data-right branches
+// right-ascending; "Squidsort" section: the data decides, as in Octosort's
+// lazily enforced order of the "Full adaptivity" section).  The in-place merge
+// reads the outer child's run, which lies under the node's output, from its
+// inner end, so a node always has its outer child's orientation; the inner
+// child lies in the buffer and is read in whichever direction the node needs.
 
 struct FrogNode {
     int64_t n, b, r, s;
-    int32_t side, pad;
+    int32_t side, ori;
 };
 
 __host__ __device__ __forceinline__ void frog_split(const FrogNode& p, FrogNode& L, FrogNode& R)
@@ -357,7 +374,7 @@ __host__ __device__ __forceinline__ void frog_split(const FrogNode& p, FrogNode&
     int64_t b_outer = n_outer / 2, b_inner = p.b - b_outer;
     if (p.side == 0) { L.n = n_outer; L.b = b_outer; R.n = n_inner; R.b = b_inner; }
     else             { L.n = n_inner; L.b = b_inner; R.n = n_outer; R.b = b_outer; }
-    L.side = 0; R.side = 1; L.pad = R.pad = 0;
+    L.side = 0; R.side = 1; L.ori = R.ori = 0;
     L.r = p.r; R.r = p.r + L.n + L.b;
     L.s = p.s; R.s = p.s + L.n;
 }
@@ -383,7 +400,7 @@ static __global__ void frog_plan_kernel(FrogNode* nodes, int64_t n, int D)
     int d = 63 - __clzll(idx + 1);
     int64_t k = idx + 1 - (1ll << d);
     FrogNode x;
-    x.n = n; x.b = n / 2; x.r = 0; x.s = 0; x.side = 0; x.pad = 0;
+    x.n = n; x.b = n / 2; x.r = 0; x.s = 0; x.side = 0; x.ori = 0;
     for (int lvl = d - 1; lvl >= 0; --lvl) {
         FrogNode L, R;
         frog_split(x, L, R);
@@ -404,6 +421,9 @@ __device__ __forceinline__ int64_t find_leaf(const FrogNode* leaves, int64_t nle
     return lo;
 }
 
+// Leaf orientations of the symmetric variants (FrogNode::ori).
+enum { FROG_PLAIN = 0, FROG_GECKO = 1, FROG_SQUID = 2 };
+
 // Fused setup: every leaf's elements are read from the contiguous input, sorted
 // as a tile and written to the leaf's gapped data slots (Frogsort1 setup; the
 // destination is never left of the source).  A leaf's destination can overlap
@@ -411,11 +431,23 @@ __device__ __forceinline__ int64_t find_leaf(const FrogNode* leaves, int64_t nle
 // by ticket, each publishes "inputs loaded" right after loading, and writes only
 // once every overlapped leaf has published.  Earlier tickets never wait on later
 // ones, so the waits cannot deadlock; they are bounded anyway.
-template <int THREADS, int ITEMS>
+//
+// VARIANT picks the orientation each leaf's run is stored in (leaf_ori[leaf]
+// receives it; unused for FROG_PLAIN):
+//   FROG_PLAIN  ascending (Frogsort1);
+//   FROG_GECKO  the leaf's side: data-left leaves ascending, data-right leaves
+//               mirrored (Geckosort);
+//   FROG_SQUID  decided by the data (Squidsort): mirrored when the leaf's input
+//               is non-increasing and its first key lies strictly above its
+//               last -- the leaf-sized form of Octosort's rule for two single
+//               elements (mirrored when strictly out of order).
+// A mirrored leaf stores its stable ascending sequence right to left; the
+// result is the same stable sort whatever the orientations are.
+template <int THREADS, int ITEMS, int VARIANT = FROG_PLAIN>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS)   // <= 64 registers: 1024 threads per SM
     frog_setup_kernel(Slots sl, const FrogNode* __restrict__ leaves, int64_t nleaves, int mode,
                       int* ticket, int* loaded, int* call_err, uint64_t limit_ns,
-                      const int* presorted)
+                      const int* presorted, int* leaf_ori)
 {
     constexpr int T = THREADS * ITEMS;
     if (skip_all(presorted)) return;
@@ -439,6 +471,15 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)   // <= 64 registers:
     }
     __syncthreads();
     if (t == 0) st_release(&loaded[leaf], 1);
+    int ori = 0;
+    if (VARIANT == FROG_GECKO) ori = x.side;
+    if (VARIANT == FROG_SQUID) {
+        bool nonincr = true;
+        for (int i = t; i + 1 < nv; i += THREADS) nonincr &= sm.k[pidx(i)] >= sm.k[pidx(i + 1)];
+        nonincr = __syncthreads_and(nonincr);
+        ori = (nonincr && nv >= 2 && sm.k[pidx(0)] > sm.k[pidx(nv - 1)]) ? 1 : 0;
+    }
+    if (VARIANT != FROG_PLAIN && t == 0) leaf_ori[leaf] = ori;
     block_sort_smem<THREADS, ITEMS>(sm, nv);
     const int64_t dslot = frog_data_slot(x);
     if (t == 0) {
@@ -457,10 +498,28 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)   // <= 64 registers:
     for (int j = 0; j < ITEMS; ++j) {
         int i = t + j * THREADS;
         if (i < nv) {
-            *sl.kp(dslot + i) = sm.k[pidx(i)];
-            if (sl.v0) *sl.vp(dslot + i) = sm.v[pidx(i)];
+            const int64_t d = dslot + (ori ? nv - 1 - i : i);
+            *sl.kp(d) = sm.k[pidx(i)];
+            if (sl.v0) *sl.vp(d) = sm.v[pidx(i)];
         }
     }
+}
+
+// Orientation of every node of the Frogsort1 tree (heap order, depths 0..D)
+// from its leaves' (symmetric variants): a node takes its outer child's
+// orientation, and the outer child of a data-left node is its left child,
+// which is data-left again, so a data-left node has its leftmost leaf's
+// orientation and a data-right node its rightmost leaf's.
+static __global__ void frog_orient_kernel(FrogNode* nodes, int D, const int* __restrict__ leaf_ori,
+                                          const int* presorted)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (2ll << D) - 1 || skip_all(presorted)) return;
+    const int d = 63 - __clzll(idx + 1);
+    const int64_t k = idx + 1 - (1ll << d);
+    const int sh = D - d;
+    const int64_t leaf = nodes[idx].side == 0 ? (k << sh) : ((k + 1) << sh) - 1;
+    nodes[idx].ori = leaf_ori[leaf];
 }
 
 // The chunks of a level's nodes are numbered node by node: node k's chunks
@@ -489,7 +548,17 @@ __device__ __forceinline__ void frog_locate(int64_t idx, const int64_t* __restri
 }
 
 // splits[base(k) + c] = co-rank (left-run elements) of output c*CHUNK of node k.
-static __global__ void frog_partition_kernel(Slots sl, const FrogNode* __restrict__ level,
+//
+// SYM (nodes of either orientation): the merge runs in slot order.  An
+// ascending node takes its left run first on ties; a mirrored node stores the
+// sequence right to left, so in slot order its larger keys come first and, of
+// equal keys, the later one (the right run's).  So the first run F is the
+// left child of an ascending node and the right child of a mirrored one, keys
+// are compared after XOR with the node's mask (all ones when mirrored), F wins
+// ties, and a child whose orientation differs from the node's is read from its
+// far end.  splits then count F's elements.
+template <bool SYM>
+__global__ void frog_partition_kernel(Slots sl, const FrogNode* __restrict__ level,
                                       const FrogNode* __restrict__ child, int64_t nnodes, int64_t nch,
                                       const int64_t* __restrict__ cstart, int64_t total, int64_t* splits,
                                       const int* presorted)
@@ -500,9 +569,30 @@ static __global__ void frog_partition_kernel(Slots sl, const FrogNode* __restric
     frog_locate(idx, cstart, nnodes, nch, k, c, base, nchk);
     FrogNode x = level[k], L = child[2 * k], R = child[2 * k + 1];
     int64_t diag = imin64(c * CHUNK, x.n);
-    int64_t ra = frog_data_slot(L), rb = frog_data_slot(R);
-    splits[idx] = merge_path(diag, L.n, R.n, [&](int64_t i) { return *sl.kp(ra + i); },
-                             [&](int64_t j) { return *sl.kp(rb + j); });
+    if (!SYM) {
+        int64_t ra = frog_data_slot(L), rb = frog_data_slot(R);
+        splits[idx] = merge_path(diag, L.n, R.n, [&](int64_t i) { return *sl.kp(ra + i); },
+                                 [&](int64_t j) { return *sl.kp(rb + j); });
+        return;
+    }
+    const bool desc = x.ori != 0;
+    const FrogNode F = desc ? R : L, S = desc ? L : R;
+    const uint64_t mask = desc ? ~0ull : 0ull;
+    const int64_t fd = frog_data_slot(F), sd = frog_data_slot(S);
+    const bool rf = F.ori != x.ori, rs = S.ori != x.ori;
+    splits[idx] = merge_path(
+        diag, F.n, S.n, [&](int64_t i) { return *sl.kp(rf ? fd + F.n - 1 - i : fd + i) ^ mask; },
+        [&](int64_t j) { return *sl.kp(rs ? sd + S.n - 1 - j : sd + j) ^ mask; });
+}
+
+// Squidsort's one final reversal: a root stored mirrored is reversed in place
+// after its last level (the root is data-left: slots [0, n)).  Skipped when the
+// whole sort was (presorted or reversed input, or an error).
+static __global__ void reverse_root_kernel(uint64_t* keys, uint32_t* vals, int64_t n, const FrogNode* root,
+                                           const int* ctl)
+{
+    if (skip_all(ctl) || root->ori == 0) return;
+    reverse_body(keys, vals, n);
 }
 
 // One in-place symmetric merge level (kernel: frog_merge_tma_kernel).  A

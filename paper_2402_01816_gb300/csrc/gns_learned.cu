@@ -1267,7 +1267,7 @@ bool half_plan(int64_t n, bool with_vals, HalfPlan& P)
     P.n = n;
     P.b = n / 2 + HALF_EXTRA;
     FrogNode root;
-    root.n = n; root.b = P.b; root.r = 0; root.s = 0; root.side = 0; root.pad = 0;
+    root.n = n; root.b = P.b; root.r = 0; root.s = 0; root.side = 0; root.ori = 0;
     P.nodes[0] = root;
     frog_split(P.nodes[0], P.nodes[1], P.nodes[2]);
     frog_split(P.nodes[1], P.nodes[3], P.nodes[4]);

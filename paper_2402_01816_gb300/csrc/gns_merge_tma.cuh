@@ -126,11 +126,14 @@ struct StagedChunk {
 // Everything a ticket's merge needs, precomputed by frog_items_kernel so that
 // the merge loop issues its copies after one independent load.
 struct FrogItem {
-    int64_t ra, rb;        // slot of the first element of the left / right slice
+    int64_t ra, rb;        // lowest slot of the first / second slice (left / right run unless SYM)
     int64_t oslot;         // slot of the first output
     int32_t na, nb;        // slice lengths (0, 0: nothing to do)
     int32_t dep_lo, dep_hi;   // tickets whose loads must precede the store (dep_hi < dep_lo: none)
+    int32_t flags;         // SYM levels: FI_REV_A / FI_REV_B (slice read from its far end), FI_DESC
+    int32_t pad;
 };
+enum { FI_REV_A = 1, FI_REV_B = 2, FI_DESC = 4 };
 
 // Range [lo, hi] of the chunks of node k that read the run elements chunk c
 // overwrites (hi < lo: none).  A data-left node overwrites left-run indices
@@ -191,6 +194,62 @@ __device__ __forceinline__ int2 frog_dep_range(int64_t c, const FrogNode& x, con
     return r;
 }
 
+// frog_dep_range for nodes of either orientation (SYM levels).  The outer
+// child's run lies under the output and is never read reversed; its consumed
+// index i sits at output index i + off (off = 0 for a data-left node, the
+// inner child's size for a data-right one) and every element moves towards
+// the node's outer end, so only later chunks (data-left) or earlier chunks
+// (data-right) can read what chunk c overwrites.  The outer run is the first
+// run F (whose counts the splits hold) or the second, by orientation.
+__device__ __forceinline__ int2 frog_dep_range_sym(int64_t c, const FrogNode& x, int64_t nF, int64_t n_outer,
+                                                   bool outer_is_f, const int64_t* sp, int C)
+{
+    int2 r = make_int2(0, -1);
+    const int64_t w0 = c * C, w1 = imin64(w0 + C, x.n);
+    if (w0 >= x.n) return r;
+    const int64_t last = (x.n - 1) / C;
+    auto f_end = [&](int64_t q) { return q == last ? nF : sp[q + 1]; };
+    auto o_beg = [&](int64_t q) { return outer_is_f ? sp[q] : q * C - sp[q]; };
+    auto o_end = [&](int64_t q) { return outer_is_f ? f_end(q) : imin64((q + 1) * C, x.n) - f_end(q); };
+    const int64_t off = x.side == 0 ? 0 : x.n - n_outer;
+    const int64_t lo_o = imax64(w0 - off, 0), hi_o = imin64(w1 - off, n_outer);
+    if (lo_o >= hi_o) return r;
+    if (x.side == 0) {
+        if (c >= last) return r;
+        int64_t lo = c + 1, hi = last;                  // first q > c with o_end(q) > lo_o
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (o_end(mid) > lo_o) hi = mid;
+            else lo = mid + 1;
+        }
+        if (o_beg(lo) >= hi_o) return r;
+        int64_t lo2 = lo, hi2 = last;                   // last q with o_beg(q) < hi_o
+        while (lo2 < hi2) {
+            const int64_t mid = (lo2 + hi2 + 1) >> 1;
+            if (o_beg(mid) < hi_o) lo2 = mid;
+            else hi2 = mid - 1;
+        }
+        r = make_int2((int)lo, (int)lo2);
+    } else {
+        if (c <= 0 || o_beg(0) >= hi_o) return r;
+        int64_t lo = 0, hi = c - 1;                     // last q < c with o_beg(q) < hi_o
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (o_beg(mid) < hi_o) lo = mid;
+            else hi = mid - 1;
+        }
+        if (o_end(lo) <= lo_o) return r;
+        int64_t lo2 = 0, hi2 = lo;                      // first q with o_end(q) > lo_o
+        while (lo2 < hi2) {
+            const int64_t mid = (lo2 + hi2) >> 1;
+            if (o_end(mid) > lo_o) hi2 = mid;
+            else lo2 = mid + 1;
+        }
+        r = make_int2((int)lo2, (int)lo);
+    }
+    return r;
+}
+
 // items[tk] for every ticket tk of a level (after the partition, before the
 // merge): ticket tk = base(k) + local (frog_locate) is chunk c = nchk - 1 -
 // local of a data-left node k and chunk c = local of a data-right one.
@@ -203,11 +262,11 @@ __device__ __forceinline__ int2 frog_dep_range(int64_t c, const FrogNode& x, con
 // section: at most half the data moves).  Such a chunk's inputs are its own
 // output slots, which no other chunk writes, so no chunk waits on it.  Off on
 // the level that decodes the keys, where every element is rewritten.
-static __global__ void frog_items_kernel(const FrogNode* __restrict__ level, const FrogNode* __restrict__ child,
-                                         int64_t nnodes, int64_t nch, const int64_t* __restrict__ cstart,
-                                         int64_t total, const int64_t* __restrict__ splits,
-                                         FrogItem* __restrict__ items, int* call_err, const int* presorted,
-                                         int skip_identity)
+template <bool SYM>
+__global__ void frog_items_kernel(const FrogNode* __restrict__ level, const FrogNode* __restrict__ child,
+                                  int64_t nnodes, int64_t nch, const int64_t* __restrict__ cstart, int64_t total,
+                                  const int64_t* __restrict__ splits, FrogItem* __restrict__ items, int* call_err,
+                                  const int* presorted, int skip_identity)
 {
     const int64_t tk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (tk >= total || skip_all(presorted)) return;
@@ -220,27 +279,41 @@ static __global__ void frog_items_kernel(const FrogNode* __restrict__ level, con
     it.na = it.nb = 0;
     it.dep_lo = 0;
     it.dep_hi = -1;
+    it.flags = 0;
+    it.pad = 0;
     const int64_t w0 = c * CHUNK;
     if (w0 < x.n) {
         const int64_t w1 = imin64(w0 + CHUNK, x.n);
         const FrogNode L = child[2 * k], R = child[2 * k + 1];
+        // SYM: slice A is the first run F, slice B the second (frog_partition_kernel)
+        const bool desc = SYM && x.ori != 0;
+        const FrogNode& F = desc ? R : L;
+        const FrogNode& S = desc ? L : R;
+        const bool rf = SYM && F.ori != x.ori, rs = SYM && S.ori != x.ori;
         const int64_t* sp = splits + base;
         const int64_t a0 = sp[c];
-        const int64_t a1 = (w1 == x.n) ? L.n : sp[c + 1];
+        const int64_t a1 = (w1 == x.n) ? F.n : sp[c + 1];
         const int64_t na = a1 - a0, nb = (w1 - a1) - (w0 - a0);
-        if (na < 0 || nb < 0 || na + nb > CHUNK || a0 < 0 || a1 > L.n) {   // splits inconsistent
+        if (na < 0 || nb < 0 || na + nb > CHUNK || a0 < 0 || a1 > F.n) {   // splits inconsistent
             atomicCAS(call_err, 0, GNS_ERR_INTERNAL);
         } else {
             it.na = (int32_t)na;
             it.nb = (int32_t)nb;
-            it.ra = frog_data_slot(L) + a0;
-            it.rb = frog_data_slot(R) + (w0 - a0);
+            it.ra = rf ? frog_data_slot(F) + F.n - a1 : frog_data_slot(F) + a0;
+            it.rb = rs ? frog_data_slot(S) + S.n - (w1 - a1) : frog_data_slot(S) + (w0 - a0);
             it.oslot = frog_data_slot(x) + w0;
-            const bool identity = (nb == 0 && it.ra == it.oslot) || (na == 0 && it.rb == it.oslot);
+            it.flags = (rf ? FI_REV_A : 0) | (rs ? FI_REV_B : 0) | (desc ? FI_DESC : 0);
+            const bool identity = (nb == 0 && !rf && it.ra == it.oslot) || (na == 0 && !rs && it.rb == it.oslot);
             if (skip_identity && identity) {
                 it.na = it.nb = 0;
             } else {
-                const int2 r = frog_dep_range(c, x, L, R, sp, CHUNK);
+                int2 r;
+                if (SYM) {
+                    const FrogNode& O = x.side == 0 ? L : R;
+                    r = frog_dep_range_sym(c, x, F.n, O.n, (x.side == 0) != desc, sp, CHUNK);
+                } else {
+                    r = frog_dep_range(c, x, L, R, sp, CHUNK);
+                }
                 if (r.x <= r.y) {
                     it.dep_lo = (int32_t)(x.side == 0 ? base + nchk - 1 - r.y : base + r.x);
                     it.dep_hi = (int32_t)(x.side == 0 ? base + nchk - 1 - r.x : base + r.y);

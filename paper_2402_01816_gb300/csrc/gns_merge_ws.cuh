@@ -67,6 +67,7 @@ struct WsLoad {
     int decode;
     int64_t tk;                   // item index (in-place level: its "loaded" flag)
     int32_t dep_lo, dep_hi;       // items whose loads must precede the store
+    int flags;                    // FrogItem::flags (symmetric in-place levels)
 };
 
 // What the consumers need of a staged item.
@@ -76,6 +77,7 @@ struct WsInfo {
     int decode;
     int end;                      // no more items
     int64_t tk;                   // in-place level: the item's "loaded" flag
+    int flags;                    // FrogItem::flags (symmetric in-place levels)
 };
 
 // What the producer keeps of a staged item until its store.
@@ -206,6 +208,79 @@ __device__ __forceinline__ int merge_staged_ct(const InStage<C>& st, const Stage
         }
     }
     return cnt - diag < ITEMS ? cnt - diag : ITEMS;
+}
+
+// merge_staged_ct for the symmetric in-place levels (nodes of either
+// orientation, frog_partition_kernel): slice A is the first run, and a slice
+// flagged FI_REV_* is consumed from its highest slot down; keys are compared
+// after XOR with the mask (all ones for a mirrored node, whose slot order puts
+// larger keys first), the stored keys are unchanged.  As in merge_staged_ct a
+// head is reloaded without a bounds test: one word past the end of a run, which
+// for a reversed slice is the word below it -- the symmetric levels stage
+// their slices from word SYM_STAGE_K0 on, so that word is inside the stage.
+// (Items without flags take merge_staged_ct itself.)
+constexpr int SYM_STAGE_K0 = 2, SYM_STAGE_V0 = 4;   // first staged key / payload word (16-byte aligned)
+template <int C, int ITEMS>
+__device__ __forceinline__ int merge_staged_sym(const InStage<C>& st, const StagedChunk& g, int flags,
+                                                uint64_t (&k)[ITEMS], uint32_t (&v)[ITEMS], bool has_vals, int ct)
+{
+    const int na = g.na, nb = g.nb, cnt = na + nb;
+    const int diag = ct * ITEMS;
+    if (diag >= cnt) return 0;
+    const uint64_t mask = (flags & FI_DESC) ? ~0ull : 0ull;
+    const int sa = (flags & FI_REV_A) ? -1 : 1, sb = (flags & FI_REV_B) ? -1 : 1;
+    const int pa = (flags & FI_REV_A) ? g.ka + na - 1 : g.ka, pb = (flags & FI_REV_B) ? g.kb + nb - 1 : g.kb;
+    const int qa = (flags & FI_REV_A) ? g.va + na - 1 : g.va, qb = (flags & FI_REV_B) ? g.vb + nb - 1 : g.vb;
+    int lo = diag - nb > 0 ? diag - nb : 0, hi = diag < na ? diag : na;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((st.k[pa + sa * mid] ^ mask) <= (st.k[pb + sb * (diag - 1 - mid)] ^ mask)) lo = mid + 1;
+        else hi = mid;
+    }
+    int i = lo, j = diag - lo;
+    int xa = pa + sa * i, xb = pb + sb * j;          // shared index of each run's head
+    int ya = qa + sa * i, yb = qb + sb * j;
+    uint64_t ka = i < na ? st.k[xa] ^ mask : ~0ull;
+    uint64_t kb = j < nb ? st.k[xb] ^ mask : ~0ull;
+#pragma unroll
+    for (int x = 0; x < ITEMS; ++x) {
+        const bool takeA = (j >= nb) || (i < na && ka <= kb);
+        k[x] = (takeA ? ka : kb) ^ mask;
+        if (has_vals) v[x] = st.v[takeA ? ya : yb];
+        if (takeA) {
+            ++i;
+            xa += sa;
+            ya += sa;
+            ka = st.k[xa] ^ mask;
+        } else {
+            ++j;
+            xb += sb;
+            yb += sb;
+            kb = st.k[xb] ^ mask;
+        }
+    }
+    return cnt - diag < ITEMS ? cnt - diag : ITEMS;
+}
+
+// copy_staged_striped for the symmetric in-place levels: the one non-empty
+// slice, consumed from its far end when flagged.
+template <int C, int ITEMS, int CT>
+__device__ __forceinline__ void copy_staged_sym(const InStage<C>& st, const StagedChunk& g, int flags,
+                                                uint64_t (&k)[ITEMS], uint32_t (&v)[ITEMS], bool has_vals, int ct)
+{
+    const bool from_a = g.nb == 0;
+    const int cnt = g.na + g.nb;
+    const bool rev = (flags & (from_a ? FI_REV_A : FI_REV_B)) != 0;
+    const int bk = from_a ? g.ka : g.kb, bv = from_a ? g.va : g.vb;
+#pragma unroll
+    for (int x = 0; x < ITEMS; ++x) {
+        const int e = ct + x * CT;
+        if (e < cnt) {
+            const int q = rev ? cnt - 1 - e : e;
+            k[x] = st.k[bk + q];
+            if (has_vals) v[x] = st.v[bv + q];
+        }
+    }
 }
 
 // A chunk whose outputs all come from one run (one slice empty: presorted
@@ -356,7 +431,7 @@ __device__ __forceinline__ void ws_shifts(const uint64_t* dk, const uint32_t* dv
 
 // The pipeline.  Src::next(WsLoad&) hands the producer its next item (false:
 // none left).  FLAGS: publish/await "inputs loaded" flags (in-place level).
-template <int CT, int ITEMS, int S, bool FLAGS, typename Src>
+template <int CT, int ITEMS, int S, bool FLAGS, bool SYM, typename Src>
 __device__ __forceinline__ void ws_merge(Src& src, const Slots& sl, bool has_vals, int mode, int* call_err,
                                          uint64_t limit_ns, int* loaded, int epoch, int64_t skip_ticket)
 {
@@ -439,9 +514,11 @@ __device__ __forceinline__ void ws_merge(Src& src, const Slots& sl, bool has_val
                         inf.g.na = na;
                         inf.g.nb = nb;
                         InStage<C>& st = sm.in[q];
-                        unsigned bytes = stage_slice_1t(st.k, st.v, 0, 0, L.ak, L.av, na, &full[q], inf.g.ka,
-                                                        inf.g.va, L.plain_a ? &sl : nullptr, L.slot_a, has_vals,
-                                                        L.ak_end, L.av_end);
+                        // symmetric levels: two spare key words below slice A (merge_staged_sym)
+                        unsigned bytes = stage_slice_1t(st.k, st.v, SYM ? SYM_STAGE_K0 : 0, SYM ? SYM_STAGE_V0 : 0,
+                                                        L.ak, L.av, na, &full[q], inf.g.ka, inf.g.va,
+                                                        L.plain_a ? &sl : nullptr, L.slot_a, has_vals, L.ak_end,
+                                                        L.av_end);
                         const int s0k = (inf.g.ka + na + 1) & ~1;     // 16-byte boundary after slice A
                         const int s0v = (inf.g.va + na + 3) & ~3;
                         bytes += stage_slice_1t(st.k, st.v, s0k, s0v, L.bk, L.bv, nb, &full[q], inf.g.kb, inf.g.vb,
@@ -458,6 +535,7 @@ __device__ __forceinline__ void ws_merge(Src& src, const Slots& sl, bool has_val
                         inf.decode = L.decode;
                         inf.end = 0;
                         inf.tk = L.tk;
+                        inf.flags = L.flags;
                         info[q] = inf;
                         sdn[q] = L.dep_lo;
                         sdh[q] = L.dep_hi;
@@ -506,8 +584,13 @@ __device__ __forceinline__ void ws_merge(Src& src, const Slots& sl, bool has_val
         int m = 0;
         const bool one = inf.g.na == 0 || inf.g.nb == 0;   // uniform: from the stage's record
         if (ok && !inf.end) {
-            if (one) copy_staged_striped<C, ITEMS, CT>(sm.in[s], inf.g, k, v, has_vals, ct);
-            else m = merge_staged_ct<C, ITEMS>(sm.in[s], inf.g, k, v, has_vals, ct);
+            if (SYM && inf.flags != 0) {       // uniform: from the stage's record
+                if (one) copy_staged_sym<C, ITEMS, CT>(sm.in[s], inf.g, inf.flags, k, v, has_vals, ct);
+                else m = merge_staged_sym<C, ITEMS>(sm.in[s], inf.g, inf.flags, k, v, has_vals, ct);
+            } else {
+                if (one) copy_staged_striped<C, ITEMS, CT>(sm.in[s], inf.g, k, v, has_vals, ct);
+                else m = merge_staged_ct<C, ITEMS>(sm.in[s], inf.g, k, v, has_vals, ct);
+            }
         }
         named_bar_sync(1, CT);                       // every consumer is done reading the stage
         if (s_cfail || inf.end) break;               // uniform: written before the barrier
@@ -681,6 +764,7 @@ struct PlainLevelSrc {
         L.tk = 0;
         L.dep_lo = 0;
         L.dep_hi = -1;
+        L.flags = 0;
         b += gridDim.x;
         return true;
     }
@@ -727,6 +811,7 @@ struct FrogLevelSrc {
         L.tk = tk;
         L.dep_lo = it.dep_lo;
         L.dep_hi = it.dep_hi;
+        L.flags = it.flags;
         return true;
     }
 };
@@ -743,7 +828,8 @@ __global__ void __launch_bounds__(WS_CONSUMERS + 32, ws_ctas_per_sm<S>())
     ws_merge_out<WS_CONSUMERS, WS_ITEMS, S>(src, sv != nullptr, mode, call_err, limit_ns);
 }
 
-template <int S>
+// SYM: the symmetric variants' levels (nodes of either orientation).
+template <int S, bool SYM = false>
 __global__ void __launch_bounds__(WS_CONSUMERS + 32, ws_frog_ctas_per_sm<S>())
     frog_merge_ws_kernel(Slots sl, const FrogItem* __restrict__ items, int64_t total, int mode, int decode_out,
                          int* ticket, int* loaded, int epoch, int* call_err, uint64_t limit_ns, int64_t skip_ticket,
@@ -751,8 +837,8 @@ __global__ void __launch_bounds__(WS_CONSUMERS + 32, ws_frog_ctas_per_sm<S>())
 {
     if (skip_all(presorted)) return;
     FrogLevelSrc src{sl, items, total, ticket, decode_out};
-    ws_merge<WS_CONSUMERS, WS_ITEMS, S, true>(src, sl, sl.v0 != nullptr, mode, call_err, limit_ns, loaded, epoch,
-                                              skip_ticket);
+    ws_merge<WS_CONSUMERS, WS_ITEMS, S, true, SYM>(src, sl, sl.v0 != nullptr, mode, call_err, limit_ns, loaded,
+                                                   epoch, skip_ticket);
 }
 
 }  // namespace gns

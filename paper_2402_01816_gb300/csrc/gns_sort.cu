@@ -72,7 +72,7 @@ void frog2_split(const FrogNode& p, int64_t pn, FrogNode& L, FrogNode& R)
     const int64_t b_outer = n_outer * pn / FROG2_DEN, b_inner = p.b - b_outer;
     if (p.side == 0) { L.n = n_outer; L.b = b_outer; R.n = n_inner; R.b = b_inner; }
     else             { L.n = n_inner; L.b = b_inner; R.n = n_outer; R.b = b_outer; }
-    L.side = 0; R.side = 1; L.pad = R.pad = 0;
+    L.side = 0; R.side = 1; L.ori = R.ori = 0;
     L.r = p.r; R.r = p.r + L.n + L.b;
     L.s = p.s; R.s = p.s + L.n;
 }
@@ -93,7 +93,7 @@ Frog2Plan frog2_plan(int64_t n, int64_t pn)
 {
     Frog2Plan P;
     std::vector<FrogNode> cur(1), nxt;
-    cur[0].n = n; cur[0].b = n * pn / FROG2_DEN; cur[0].r = 0; cur[0].s = 0; cur[0].side = 0; cur[0].pad = 0;
+    cur[0].n = n; cur[0].b = n * pn / FROG2_DEN; cur[0].r = 0; cur[0].s = 0; cur[0].side = 0; cur[0].ori = 0;
     while (!cur.empty()) {
         nxt.clear();
         const int64_t first = (int64_t)P.internal.size(), first_c = (int64_t)P.cstart.size();
@@ -193,7 +193,7 @@ const Frog2Dev* frog2_get(int64_t n, int64_t pn)
 
 struct Layout {
     // control words (ints): [0..1] presorted flags, [2] call error
-    size_t ctl, bufk, bufv, splits, items, nodes, flags, tickets, total;
+    size_t ctl, bufk, bufv, splits, items, nodes, flags, tickets, leaf_ori, total;
     size_t flags_bytes, tickets_bytes;
     int L, D;
 };
@@ -237,6 +237,7 @@ Layout make_layout(int64_t n, double bf, bool with_vals, const Frog2Plan* plan)
         o.items = off; off += align256((size_t)max_split * sizeof(FrogItem));
         o.flags = off; o.flags_bytes = align256((size_t)nflags * 4); off += o.flags_bytes;
         o.tickets = off; o.tickets_bytes = align256((size_t)(D + 1) * 4); off += o.tickets_bytes;
+        o.leaf_ori = off; off += align256((size_t)(1ll << D) * 4);   // symmetric variants
     }
     o.total = off;
     return o;
@@ -254,13 +255,18 @@ void init_attributes()
 {
     g_attr_once.run([] {
         set_smem(tile_sort_kernel<SORT_THREADS, SORT_ITEMS>, kSmemTile);
-        set_smem(frog_setup_kernel<SORT_THREADS, SORT_ITEMS>, kSmemTile);
+        set_smem(frog_setup_kernel<SORT_THREADS, SORT_ITEMS, FROG_PLAIN>, kSmemTile);
+        set_smem(frog_setup_kernel<SORT_THREADS, SORT_ITEMS, FROG_GECKO>, kSmemTile);
+        set_smem(frog_setup_kernel<SORT_THREADS, SORT_ITEMS, FROG_SQUID>, kSmemTile);
         set_smem(merge_pass_ws_kernel<2>, ws_smem_out<2>());
         set_smem(merge_pass_ws_kernel<3>, ws_smem_out<3>());
         set_smem(merge_pass_ws_kernel<4>, ws_smem_out<4>());
         set_smem(frog_merge_ws_kernel<2>, ws_smem<2>());
         set_smem(frog_merge_ws_kernel<3>, ws_smem<3>());
         set_smem(frog_merge_ws_kernel<4>, ws_smem<4>());
+        set_smem(frog_merge_ws_kernel<2, true>, ws_smem<2>());
+        set_smem(frog_merge_ws_kernel<3, true>, ws_smem<3>());
+        set_smem(frog_merge_ws_kernel<4, true>, ws_smem<4>());
     });
 }
 
@@ -332,16 +338,18 @@ cudaError_t launch_plain_level_ws(const uint64_t* sk, const uint32_t* sv, uint64
                   ws_smem_out<S>(), s, sk, sv, dk, dv, n, w, nblocks, splits, mode, decode, call_err, limit, skip);
 }
 
-template <int S>
+template <int S, bool SYM>
 cudaError_t launch_frog_level_ws(const Slots& sl, const FrogItem* items, int64_t total, int mode, int decode,
                                  int* ticket, int* loaded, int epoch, int* call_err, uint64_t limit,
                                  int64_t skip_ticket, const int* skip, cudaStream_t s)
 {
     static int64_t caps[64] = {};
-    const int64_t cap = resident_ctas_cached(caps, frog_merge_ws_kernel<S>, WS_CONSUMERS + 32, ws_smem<S>());
+    const int64_t cap =
+        resident_ctas_cached(caps, frog_merge_ws_kernel<S, SYM>, WS_CONSUMERS + 32, ws_smem<S>());
     const int64_t grid = imin(total, cap);
-    return launch(K_FROG_MERGE, frog_merge_ws_kernel<S>, dim3((unsigned)grid), dim3(WS_CONSUMERS + 32), ws_smem<S>(),
-                  s, sl, items, total, mode, decode, ticket, loaded, epoch, call_err, limit, skip_ticket, skip);
+    return launch(K_FROG_MERGE, frog_merge_ws_kernel<S, SYM>, dim3((unsigned)grid), dim3(WS_CONSUMERS + 32),
+                  ws_smem<S>(), s, sl, items, total, mode, decode, ticket, loaded, epoch, call_err, limit,
+                  skip_ticket, skip);
 }
 
 cudaError_t launch_plain_level(const uint64_t* sk, const uint32_t* sv, uint64_t* dk, uint32_t* dv, int64_t n,
@@ -360,14 +368,21 @@ cudaError_t launch_plain_level(const uint64_t* sk, const uint32_t* sv, uint64_t*
 
 cudaError_t launch_frog_level(const Slots& sl, const FrogItem* items, int64_t total, int mode, int decode,
                               int* ticket, int* loaded, int epoch, int* call_err, uint64_t limit, int64_t skip_ticket,
-                              const int* skip, cudaStream_t s)
+                              const int* skip, cudaStream_t s, bool sym = false)
 {
 #define GNS_FROG_ARGS sl, items, total, mode, decode, ticket, loaded, epoch, call_err, limit, skip_ticket, skip, s
+    if (sym) {
+        switch (frog_pipe()) {
+        case PIPE_WS2: return launch_frog_level_ws<2, true>(GNS_FROG_ARGS);
+        case PIPE_WS4: return launch_frog_level_ws<4, true>(GNS_FROG_ARGS);
+        default: return launch_frog_level_ws<3, true>(GNS_FROG_ARGS);
+        }
+    }
     switch (frog_pipe()) {
-    case PIPE_WS2: return launch_frog_level_ws<2>(GNS_FROG_ARGS);
-    case PIPE_WS3: return launch_frog_level_ws<3>(GNS_FROG_ARGS);
-    case PIPE_WS4: return launch_frog_level_ws<4>(GNS_FROG_ARGS);
-    default: return launch_frog_level_ws<2>(GNS_FROG_ARGS);
+    case PIPE_WS2: return launch_frog_level_ws<2, false>(GNS_FROG_ARGS);
+    case PIPE_WS3: return launch_frog_level_ws<3, false>(GNS_FROG_ARGS);
+    case PIPE_WS4: return launch_frog_level_ws<4, false>(GNS_FROG_ARGS);
+    default: return launch_frog_level_ws<2, false>(GNS_FROG_ARGS);
     }
 #undef GNS_FROG_ARGS
 }
@@ -465,7 +480,10 @@ done:
     return rc;
 }
 
-int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, cudaStream_t s)
+// variant (Frogsort1's tree only, bf in [0.5, 1)): FROG_PLAIN = Frogsort1,
+// FROG_GECKO = Geckosort1, FROG_SQUID = Squidsort1 (frog_setup_kernel).
+int sort_device_variant(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, int variant,
+                        cudaStream_t s)
 {
     if (n <= 1) return GNS_OK;
     if (bf >= 1.0 || n <= TILE) {
@@ -517,9 +535,9 @@ int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, 
         const uint64_t limit = wait_limit_ns();
         GNS_TRY(cudaMemsetAsync(flags, 0, lay.flags_bytes + lay.tickets_bytes, s));
         const int64_t nleaves = (int64_t)plan.leaves.size();
-        GNS_TRY(launch(K_FROG_SETUP, frog_setup_kernel<SORT_THREADS, SORT_ITEMS>, dim3((unsigned)nleaves),
-                       dim3(SORT_THREADS), kSmemTile, s, sl, leaves, nleaves, mode, tickets + D, flags, call_err,
-                       limit, skip));
+        GNS_TRY(launch(K_FROG_SETUP, frog_setup_kernel<SORT_THREADS, SORT_ITEMS, FROG_PLAIN>,
+                       dim3((unsigned)nleaves), dim3(SORT_THREADS), kSmemTile, s, sl, leaves, nleaves, mode,
+                       tickets + D, flags, call_err, limit, skip, (int*)nullptr));
         int* lflags = flags + nleaves;
         int64_t skip_ticket = take_debug_skip_publish();
         for (int d = D - 1; d >= 0; --d) {
@@ -528,9 +546,9 @@ int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, 
             const FrogNode* level = internal + f0;
             const FrogNode* child = children + 2 * f0;
             const int64_t* cs = cstart + c0;
-            GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel, dim3((unsigned)ceil_div(total, 256)), dim3(256), 0,
+            GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel<false>, dim3((unsigned)ceil_div(total, 256)), dim3(256), 0,
                            s, sl, level, child, nnodes, (int64_t)0, cs, total, splits, skip));
-            GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel, dim3((unsigned)ceil_div(total, 256)), dim3(256), 0, s,
+            GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel<false>, dim3((unsigned)ceil_div(total, 256)), dim3(256), 0, s,
                            level, child, nnodes, (int64_t)0, cs, total, (const int64_t*)splits, items, call_err,
                            skip, (int)(d != 0)));
             GNS_TRY(launch_frog_level(sl, (const FrogItem*)items, total, mode, (int)(d == 0), tickets + d, lflags,
@@ -555,9 +573,23 @@ int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, 
                        nodes, n, D));
         const int64_t nleaves = 1ll << D;
         const FrogNode* leaves = nodes + (nleaves - 1);
-        GNS_TRY(launch(K_FROG_SETUP, frog_setup_kernel<SORT_THREADS, SORT_ITEMS>, dim3((unsigned)nleaves),
-                       dim3(SORT_THREADS), kSmemTile, s, sl, leaves, nleaves, mode, tickets + D, flags, call_err,
-                       limit, skip));
+        int* leaf_ori = (int*)(ws + lay.leaf_ori);
+        const bool sym = variant != FROG_PLAIN;
+        const dim3 sgrid((unsigned)nleaves), sblock(SORT_THREADS);
+#define GNS_SETUP_ARGS sl, leaves, nleaves, mode, tickets + D, flags, call_err, limit, skip, leaf_ori
+        if (variant == FROG_GECKO)
+            GNS_TRY(launch(K_FROG_SETUP, frog_setup_kernel<SORT_THREADS, SORT_ITEMS, FROG_GECKO>, sgrid, sblock,
+                           kSmemTile, s, GNS_SETUP_ARGS));
+        else if (variant == FROG_SQUID)
+            GNS_TRY(launch(K_FROG_SETUP, frog_setup_kernel<SORT_THREADS, SORT_ITEMS, FROG_SQUID>, sgrid, sblock,
+                           kSmemTile, s, GNS_SETUP_ARGS));
+        else
+            GNS_TRY(launch(K_FROG_SETUP, frog_setup_kernel<SORT_THREADS, SORT_ITEMS, FROG_PLAIN>, sgrid, sblock,
+                           kSmemTile, s, GNS_SETUP_ARGS));
+#undef GNS_SETUP_ARGS
+        if (sym)
+            GNS_TRY(launch(K_FROG_PLAN, frog_orient_kernel, dim3((unsigned)ceil_div(total_nodes, 256)), dim3(256), 0,
+                           s, nodes, D, (const int*)leaf_ori, skip));
         int* lflags = flags + nleaves;
         int64_t skip_ticket = take_debug_skip_publish();
         for (int d = D - 1; d >= 0; --d) {
@@ -565,21 +597,37 @@ int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, 
             const int64_t nch = frog_chunks(n, d);
             const FrogNode* level = nodes + (nnodes - 1);
             const FrogNode* child = nodes + (2 * nnodes - 1);
-            GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel, dim3((unsigned)ceil_div(nnodes * nch, 256)),
-                           dim3(256), 0, s, sl, level, child, nnodes, nch, (const int64_t*)nullptr, nnodes * nch,
-                           splits, skip));
-            GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel, dim3((unsigned)ceil_div(nnodes * nch, 256)),
-                           dim3(256), 0, s, level, child, nnodes, nch, (const int64_t*)nullptr, nnodes * nch,
-                           (const int64_t*)splits, items, call_err, skip, (int)(d != 0)));
+            const dim3 pgrid((unsigned)ceil_div(nnodes * nch, 256));
+            if (sym) {
+                GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel<true>, pgrid, dim3(256), 0, s, sl, level,
+                               child, nnodes, nch, (const int64_t*)nullptr, nnodes * nch, splits, skip));
+                GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel<true>, pgrid, dim3(256), 0, s, level, child,
+                               nnodes, nch, (const int64_t*)nullptr, nnodes * nch, (const int64_t*)splits, items,
+                               call_err, skip, (int)(d != 0)));
+            } else {
+                GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel<false>, pgrid, dim3(256), 0, s, sl, level,
+                               child, nnodes, nch, (const int64_t*)nullptr, nnodes * nch, splits, skip));
+                GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel<false>, pgrid, dim3(256), 0, s, level, child,
+                               nnodes, nch, (const int64_t*)nullptr, nnodes * nch, (const int64_t*)splits, items,
+                               call_err, skip, (int)(d != 0)));
+            }
             GNS_TRY(launch_frog_level(sl, (const FrogItem*)items, nnodes * nch, mode, (int)(d == 0), tickets + d,
-                                      lflags, D - d, call_err, limit, skip_ticket, skip, s));
+                                      lflags, D - d, call_err, limit, skip_ticket, skip, s, sym));
             skip_ticket = -1;
         }
+        if (variant == FROG_SQUID)      // a mirrored root: the one final reversal
+            GNS_TRY(launch(K_REVERSE, reverse_root_kernel, dim3((unsigned)(num_sms() * 8)), dim3(256), 0, s, keys,
+                           vals, n, (const FrogNode*)nodes, (const int*)ctl));
     }
     GNS_TRY(publish_call_error(call_err, s));
 done:
     ws_free(ws, s);
     return rc;
+}
+
+int sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, cudaStream_t s)
+{
+    return sort_device_variant(keys, vals, n, mode, bf, FROG_PLAIN, s);
 }
 
 size_t frog_levels_bytes(int64_t n, int D)
@@ -615,10 +663,10 @@ int frog_levels_device(const Slots& sl, const FrogNode* nodes, int D, int mode, 
         const int64_t nch = frog_chunks(sl.n, d);
         const FrogNode* level = nodes + (nnodes - 1);
         const FrogNode* child = nodes + (2 * nnodes - 1);
-        GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel, dim3((unsigned)ceil_div(nnodes * nch, 256)),
+        GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel<false>, dim3((unsigned)ceil_div(nnodes * nch, 256)),
                        dim3(256), 0, s, sl, level, child, nnodes, nch, (const int64_t*)nullptr, nnodes * nch, splits,
                        skip));
-        GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel, dim3((unsigned)ceil_div(nnodes * nch, 256)), dim3(256), 0,
+        GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel<false>, dim3((unsigned)ceil_div(nnodes * nch, 256)), dim3(256), 0,
                        s, level, child, nnodes, nch, (const int64_t*)nullptr, nnodes * nch, (const int64_t*)splits,
                        items, call_err, skip, (int)(d != 0)));
         GNS_TRY(launch_frog_level(sl, (const FrogItem*)items, nnodes * nch, mode, (int)(d == 0), tickets + d, flags,
@@ -699,7 +747,7 @@ extern "C" int gns_frog_plan_check(int64_t n, double buffer_fraction)
     const int D = frog_leaf_depth(n);
     const int64_t total = n + n / 2;
     std::vector<FrogNode> level(1), next, leaves;
-    level[0].n = n; level[0].b = n / 2; level[0].r = 0; level[0].s = 0; level[0].side = 0; level[0].pad = 0;
+    level[0].n = n; level[0].b = n / 2; level[0].r = 0; level[0].s = 0; level[0].side = 0; level[0].ori = 0;
     for (int d = 0; d < D; ++d) {
         next.clear();
         for (const FrogNode& x : level) {

@@ -18,6 +18,12 @@ section, plus the four workload families of this library):
   ``desclocal``, ``descglobal``  -- the paper's own pattern list
 * ``presorted_runs`` blocks of 2**16; block b ascending iff b % 10 == 0,
   the others random (over a permutation of 1..n)
+* ``desc_ties``    non-increasing with every value twice: floor((n - 1 - i) / 2)
+  (descending order with ties, which a reversal would not sort stably)
+* ``desc_runs``    a random permutation of 1..n cut into runs of 2**16, each
+  sorted descending (``desclocal`` with runs of a fixed length well above a
+  tile)
+* ``desc_noise``   n..1 descending, then n/100 random transpositions
 * ``mixture``      40% exp(N(0, 2^2)); 30% Zipf(s=1.2) over 1..2**16; 30% a mix
   of 8 Gaussians (mu ~ U(-10, 10), sigma log-uniform in [0.01, 1])
 * ``segments``     log-normal segment lengths (median 2**10, clipped 16..2**20)
@@ -36,7 +42,7 @@ PAPER_PATTERNS = ("permut", "tielog2", "ascall", "asclocal", "ascglobal",
 _PATTERN_IDS = {name: i for i, name in enumerate(
     ("uniform", "permut", "ties", "asc_noise", "desc", "tielog2", "ascall", "asclocal",
      "ascglobal", "descall", "desclocal", "descglobal", "presorted_runs", "mixture",
-     "segments", "edge"))}
+     "segments", "edge", "desc_ties", "desc_runs", "desc_noise"))}
 
 
 def rng_for(pattern: str, seed: int = 0) -> np.random.Generator:
@@ -108,6 +114,24 @@ def make_keys(pattern: str, n: int, seed: int = 0) -> np.ndarray:
         for bi, s in enumerate(range(0, n, blk)):
             if bi % 10 == 0:
                 k[s:s + blk] = np.sort(k[s:s + blk])
+        return k
+    if pattern == "desc_ties":
+        return ((n - 1 - np.arange(n)) // 2).astype(np.float64)
+    if pattern == "desc_runs":
+        vals = _permutation_1n(rng, n)
+        blk = 1 << 16
+        out = np.empty(n, dtype=np.float64)
+        for s in range(0, n, blk):
+            out[s:s + blk] = np.sort(vals[s:s + blk])[::-1]
+        return out
+    if pattern == "desc_noise":
+        k = np.arange(n, 0, -1, dtype=np.float64)
+        m = n // 100
+        if n >= 2 and m > 0:
+            a = rng.integers(0, n, m)
+            b = rng.integers(0, n, m)
+            for x, y in zip(a.tolist(), b.tolist()):
+                k[x], k[y] = k[y], k[x]
         return k
     if pattern == "mixture":
         return mixture_keys(n, seed)
