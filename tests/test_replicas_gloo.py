@@ -34,7 +34,7 @@ def _rank(rank, port, out):
 
 def test_two_gloo_ranks_take_the_slowest_rank():
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(port, out), nprocs=2, join=True)
         res = dict(out)
