@@ -57,6 +57,13 @@ def parse_args():
                     help="add the 2^31-key 50%%-tier run (about 40 GB on the device, minutes of input generation)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the learned-vs-plain and batched-vs-plain comparisons")
+    ap.add_argument("--only", default=None,
+                    help="diagnostic run of one workload for profiling (no contract line): PATTERN@TIER "
+                         "(e.g. permut@100, permut@50), 'segmented' (--nseg segments) or 'learned' "
+                         "(the mixture at --n keys, full buffer)")
+    ap.add_argument("--variant", default="frog", choices=["frog", "gecko", "squid"],
+                    help="with --only PATTERN@50: the symmetric variant (gns_sort_symmetric)")
+    ap.add_argument("--nseg", type=int, default=4096, help="segments for --only segmented")
     return ap.parse_args()
 
 
@@ -245,8 +252,23 @@ def learned_vs_plain(dev, n=1 << 28):
         raise RuntimeError("device status error in learned_vs_plain")
     del keys, pay, kt, pt
     torch.cuda.empty_cache()
+    peak, peak_kind = load_peaks()
+    part_b = 66 * n                                   # histogram 10, scatter A 28, scan 2, scatter B 26 per key
+    mean_bucket = n / 4096.0
+    bucket_passes = 1 + max(0, math.ceil(math.log2(max(1.0, mean_bucket / 4096))))
+    bs_b = 24 * n * bucket_passes
+    roof = {"bound": "hbm", "peak": peak, "unit": "GB/s", "peak_kind": peak_kind,
+            "partition": {"algorithmic_bytes": part_b, "achieved": part_b / (rep["partition_ms"] / 1e3) / 1e9,
+                          "frac": part_b / (rep["partition_ms"] / 1e3) / 1e9 / peak,
+                          "bytes_model": "66 B per key: bucket pass 10, scatter A 28, digit scan 2, scatter B 26"},
+            "bucket_sort": {"algorithmic_bytes": bs_b,
+                            "achieved": bs_b / (rep["bucket_sort_ms"] / 1e3) / 1e9,
+                            "frac": bs_b / (rep["bucket_sort_ms"] / 1e3) / 1e9 / peak,
+                            "bytes_model": f"24 B per key per pass, {bucket_passes} passes of a mean-sized bucket "
+                                           "(1 tile pass + ceil(log2(L/4096)) levels)"}}
     return {"workload": "learned-splitter sort: 2^28 float64 keys (40% log-normal sigma 2, 30% Zipf s=1.2 "
                         "over 2^16 integers, 30% mix of 8 Gaussians) + uint32 index payload, 4096 buckets",
+            "roofline": roof,
             "learned_ms": t_learned, "plain_ms": t_plain, "first_stage_only_ms": t_first,
             "learned_gkeys_s": n / t_learned / 1e6, "plain_gkeys_s": n / t_plain / 1e6,
             "speedup_vs_plain": t_plain / t_learned, "speedup_vs_first_stage_only": t_first / t_learned,
@@ -296,9 +318,15 @@ def batched_vs_plain(dev, nseg=65536, per_segment_sample=2048):
         raise RuntimeError("device status error in batched_vs_plain")
     del keys, pay, off, kt, pt
     torch.cuda.empty_cache()
+    peak, peak_kind = load_peaks()
+    alg = segmented_bytes(off_h)
     return {"workload": f"batched segmented sort: {nseg} segments, log-normal lengths (median 2^10, "
                         f"clipped 16..2^20), {n} int64 keys uniform over the full range + uint32 payload",
             "segmented_ms": t_seg, "segmented_gkeys_s": n / t_seg / 1e6, "schedule": sched,
+            "roofline": {"bound": "hbm", "algorithmic_bytes": alg, "achieved": alg / (t_seg / 1e3) / 1e9,
+                         "peak": peak, "unit": "GB/s", "frac": alg / (t_seg / 1e3) / 1e9 / peak,
+                         "bytes_model": "24 B per key per executed pass: 1 tile pass + ceil(log2(L/4096)) "
+                                        "merge levels per segment of L keys", "peak_kind": peak_kind},
             "kernels_in_graph": kernels_per_call,
             "per_segment_gns_sort_ms_est": t_per_seg,
             "per_segment_estimate": f"{m} segments timed ({sub_n} keys), scaled by segment count",
@@ -437,6 +465,100 @@ def symmetric_variants(dev, n=1 << 27, host=None):
         del keys, kt, pt
         torch.cuda.empty_cache()
     return out
+
+
+def config0(dev, n=1 << 20):
+    """The small case (2^20 float64 keys uniform in [0, 1), ascending, 100%
+    buffer; L2-resident and launch-bound): the plain call, and the same keys
+    as one segment of the segmented engine, whose whole pass chain is one
+    CUDA-graph launch after its first call."""
+    import torch
+    import paper_2402_01816_gb300 as g
+    from paper_2402_01816_gb300 import inputs
+    keys = torch.from_numpy(inputs.make_keys("uniform", n, seed=0)).to(dev)
+    pay = torch.from_numpy(inputs.index_payload(n).view(np.int32)).to(dev)
+    off = torch.tensor([0, n], dtype=torch.int64, device=dev)
+    kt, pt = torch.empty_like(keys), torch.empty_like(pay)
+
+    def restore():
+        kt.copy_(keys)
+        pt.copy_(pay)
+    restore()
+    g.gns_sort(kt, pt)
+    t_plain = _time_ms(lambda: g.gns_sort(kt, pt), restore, reps=20)
+    restore()
+    g.gns_segmented_sort(kt, pt, off)                      # tunes and captures the graph
+    t_graph = _time_ms(lambda: g.gns_segmented_sort(kt, pt, off), restore, reps=20)
+    if g.gns_stream_status() != 0:
+        raise RuntimeError("device status error in config0")
+    return {"workload": "2^20 float64 keys uniform in [0,1) + uint32 index payload, ascending, 100% buffer "
+                        "(L2-resident, launch-bound)",
+            "plain_ms": t_plain, "plain_gkeys_s": n / t_plain / 1e6,
+            "one_graph_launch_ms": t_graph, "one_graph_launch_gkeys_s": n / t_graph / 1e6,
+            "note": "one_graph_launch: the keys as a single segment of gns_segmented_sort_ex, the whole "
+                    "pass chain replayed as one captured CUDA graph"}
+
+
+def segmented_bytes(off_h, tile=4096):
+    """Algorithmic bytes of the batched sort: 24 B per key per executed pass,
+    one tile pass plus ceil(log2(L / T)) merge levels for a segment of L keys."""
+    L = np.diff(off_h).astype(np.int64)
+    L = L[L > 0]
+    passes = 1 + np.ceil(np.log2(np.maximum(1.0, L / tile))).astype(np.int64)
+    return int(np.sum(24 * L * passes))
+
+
+def run_only(args):
+    """Diagnostic runs for profiling: one workload, warm-up and timed steps,
+    a short JSON line (not the benchmark contract)."""
+    import torch
+    import paper_2402_01816_gb300 as g
+    from paper_2402_01816_gb300 import build as cuda_build
+    from paper_2402_01816_gb300 import inputs
+    if not os.path.exists(cuda_build.LIB):
+        cuda_build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n = args.n
+    if args.only == "segmented":
+        keys_h, pay_h, off_h = inputs.segments(args.nseg, seed=0)
+        keys = torch.from_numpy(keys_h).to(dev)
+        pay = torch.from_numpy(pay_h.view(np.int32)).to(dev)
+        off = torch.from_numpy(off_h).to(dev)
+        fn = lambda kt, pt: g.gns_segmented_sort(kt, pt, off)          # noqa: E731
+        n = keys_h.size
+    elif args.only == "learned":
+        keys = torch.from_numpy(inputs.make_keys("mixture", n, seed=0)).to(dev)
+        pay = torch.from_numpy(inputs.index_payload(n).view(np.int32)).to(dev)
+        fn = lambda kt, pt: g.gns_learned_sort(kt, pt)                  # noqa: E731
+    else:
+        pattern, tier = args.only.split("@")
+        bf = int(tier) / 100.0
+        keys = torch.from_numpy(inputs.make_keys(pattern, n, seed=0)).to(dev)
+        pay = torch.from_numpy(inputs.index_payload(n).view(np.int32)).to(dev)
+        variant = {"frog": g.FROGSORT1, "gecko": g.GECKOSORT1, "squid": g.SQUIDSORT1}[args.variant]
+        if args.variant != "frog":
+            if bf != 0.5:
+                raise SystemExit("--variant needs a 50% tier")
+            fn = lambda kt, pt: g.gns_sort_symmetric(kt, pt, variant=variant)   # noqa: E731
+        else:
+            fn = lambda kt, pt: g.gns_sort(kt, pt, buffer_fraction=bf)          # noqa: E731
+    kt, pt = torch.empty_like(keys), torch.empty_like(pay)
+
+    def restore():
+        kt.copy_(keys)
+        pt.copy_(pay)
+    for _ in range(args.warmup):
+        restore()
+        fn(kt, pt)
+    torch.cuda.synchronize()
+    ts = [_time_ms(lambda: fn(kt, pt), restore, reps=1) for _ in range(args.steps)]
+    status = g.gns_stream_status()
+    if status != 0:
+        raise RuntimeError(f"device status {status}")
+    print(json.dumps({"only": args.only, "variant": args.variant, "n": n, "steps": args.steps,
+                      "ms": statistics.mean(ts), "gkeys_s": n / statistics.mean(ts) / 1e6,
+                      "diagnostic": True}), flush=True)
 
 
 def cpu_baseline(n_sample=1 << 25):
@@ -629,6 +751,7 @@ def run_ours(args, ws, rank, local):
         extras["learned_vs_plain"] = learned_vs_plain(dev)
         extras["batched_vs_plain"] = batched_vs_plain(dev)
         extras["symmetric_variants"] = symmetric_variants(dev, n, host)
+        extras["config0"] = config0(dev)
     if args.paper_patterns:
         extras["paper_patterns"] = paper_patterns(dev, args.n)
     if args.large:
@@ -652,6 +775,9 @@ def main():
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.only:
+        run_only(args)
         return
     run_ours(args, ws, rank, local)
 
