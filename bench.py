@@ -281,6 +281,34 @@ def learned_vs_plain(dev, n=1 << 28):
                          "report": rep_half}}
 
 
+def network_gain(dev, n=1 << 22):
+    """What the trained network changes against the first stage alone, on
+    log-normal keys (the density changes inside every first-stage interval):
+    largest bucket, overfull buckets, fit time and the whole call."""
+    import torch
+    import paper_2402_01816_gb300 as g
+    rng = np.random.default_rng(100)
+    keys = torch.from_numpy(np.exp(rng.normal(0.0, 2.0, n))).to(dev)
+    pay = torch.arange(n, dtype=torch.int64, device=dev).to(torch.int32)
+    kt, pt = torch.empty_like(keys), torch.empty_like(pay)
+
+    def restore():
+        kt.copy_(keys)
+        pt.copy_(pay)
+    out = {"workload": f"{n} log-normal float64 keys (mu 0, sigma 2) + uint32 payload, 4096 buckets"}
+    for steps in (0, 32, 256):
+        restore()
+        rep = g.gns_learned_sort(kt, pt, train_steps=steps, report=True)
+        t = _time_ms(lambda: g.gns_learned_sort(kt, pt, train_steps=steps), restore)
+        out[f"steps_{steps}"] = {"ms": t, "max_bucket": rep["max_bucket"], "overfull_buckets": rep["overfull_buckets"],
+                                 "fit_ms": rep["fit_ms"], "bucket_sort_ms": rep["bucket_sort_ms"],
+                                 "final_loss": rep["final_loss"]}
+    out["max_bucket_ratio_256_vs_first_stage"] = out["steps_256"]["max_bucket"] / out["steps_0"]["max_bucket"]
+    if g.gns_stream_status() != 0:
+        raise RuntimeError("device status error in network_gain")
+    return out
+
+
 def batched_vs_plain(dev, nseg=65536, per_segment_sample=2048):
     """gns_segmented_sort (one graph launch) against one gns_sort call per segment
     (timed on the first `per_segment_sample` segments and scaled by key count)
@@ -752,6 +780,7 @@ def run_ours(args, ws, rank, local):
         extras["batched_vs_plain"] = batched_vs_plain(dev)
         extras["symmetric_variants"] = symmetric_variants(dev, n, host)
         extras["config0"] = config0(dev)
+        extras["learned_network_gain"] = network_gain(dev)
     if args.paper_patterns:
         extras["paper_patterns"] = paper_patterns(dev, args.n)
     if args.large:

@@ -291,7 +291,7 @@ void gns_segmented_release(gns_stream_t stream);
  * over the four leaves, max_bucket and final_loss their maxima).
  */
 typedef struct {
-    int train_steps;         /* Adam steps (default 64); 0 = no network:
+    int train_steps;         /* Adam steps (default 32); 0 = no network:
                                 the first stage alone places the splitters
                                 (the method without the network)             */
     int batch;               /* samples per step, multiple of 512 (default 1024) */

@@ -196,7 +196,7 @@ class LearnedReport(ctypes.Structure):
 
 
 def gns_learned_sort(keys, payload=None, order: int = ASCENDING, buffer_fraction: float = 1.0,
-                     train_steps: int = 64, batch: int = 1024, learning_rate: float = 1e-2,
+                     train_steps: int = 32, batch: int = 1024, learning_rate: float = 1e-2,
                      overfull_factor: float = 4.0, report: bool = False, stream=None):
     """Learned-splitter stable sort of a CUDA float64 tensor; with report=True the
     call synchronises and returns the report as a dict."""

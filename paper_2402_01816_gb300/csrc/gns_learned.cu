@@ -1538,7 +1538,7 @@ int gns_mlp_train(const float* x, const float* t, int64_t m, const float* params
 int gns_learned_sort(double* keys, uint32_t* payload, int64_t n, int order, double buffer_fraction,
                      const gns_learned_params* params, gns_learned_report* report, gns_stream_t stream)
 {
-    gns_learned_params prm = {64, 1024, 1e-2f, 4.0f};
+    gns_learned_params prm = {32, 1024, 1e-2f, 4.0f};
     if (params) prm = *params;
     if (prm.train_steps < 0 || prm.batch <= 0 || prm.batch % 512 != 0 || !(prm.learning_rate > 0.f) ||
         !(prm.overfull_factor > 0.f))

@@ -243,16 +243,21 @@ def test_learned_half_buffer_edges_and_ram():
 
 def test_network_gain_over_first_stage():
     """What the trained network gains over the method without it (the
-    first-stage quantile interpolation alone): on log-normal keys, where the
-    density changes inside every first-stage interval, the largest bucket and
-    the spread of bucket sizes shrink."""
+    first-stage quantile interpolation alone), on log-normal keys, where the
+    density changes inside every first-stage interval: 256 Adam steps shrink
+    the largest bucket to at most 0.85 of the first stage's (measured 0.69 to
+    0.78 over five seeds), do not add overfull buckets, and lower the training
+    loss against a short fit.  The result is exact either way."""
     need_gpu()
-    rng = np.random.default_rng(13)
+    rng = np.random.default_rng(100)
     logn = np.exp(rng.normal(0.0, 2.0, 1 << 22))
-    trained = _learned(logn)
     first = _learned(logn, train_steps=0)
-    print("trained", trained, "first stage only", first)
-    assert trained["max_bucket"] < first["max_bucket"], (trained, first)
+    short = _learned(logn, train_steps=32)
+    trained = _learned(logn, train_steps=256)
+    print("first stage only", first, "32 steps", short, "256 steps", trained)
+    assert trained["max_bucket"] <= 0.85 * first["max_bucket"], (trained, first)
+    assert trained["overfull_buckets"] <= first["overfull_buckets"], (trained, first)
+    assert trained["final_loss"] < short["final_loss"], (trained, short)
 
 
 def test_full_learned_workload():
