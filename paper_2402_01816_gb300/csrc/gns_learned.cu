@@ -653,6 +653,8 @@ __global__ void __launch_bounds__(PART_THREADS)
     __syncthreads();
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t base = tile * PART_TILE;
+        // this tile's offset within digit t, loaded with the data (not after the barriers below)
+        const uint32_t my_cnt = t < 64 ? counts[(int64_t)t * ntiles + tile] : 0u;
         uint64_t kk[PART_ITEMS];
         uint32_t vv[PART_ITEMS];
         int bb[PART_ITEMS], dd[PART_ITEMS], rr[PART_ITEMS];
@@ -712,7 +714,7 @@ __global__ void __launch_bounds__(PART_THREADS)
             S.dstart[2 * t + 1] = excl + a;
         }
         __syncthreads();
-        if (t < 64) S.gbase[t] = S.dbase[t] + (int64_t)counts[(int64_t)t * ntiles + tile] - (int64_t)S.dstart[t];
+        if (t < 64) S.gbase[t] = S.dbase[t] + (int64_t)my_cnt - (int64_t)S.dstart[t];
 #pragma unroll
         for (int r = 0; r < PART_ITEMS; ++r) {
             if (dd[r] < 64) {

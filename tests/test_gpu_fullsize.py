@@ -51,6 +51,26 @@ def test_config_full_size(pattern, bf):
     check_sorted_stable(keys, k_out, p_out)
 
 
+@pytest.mark.parametrize("variant", ["gecko", "squid"])
+@pytest.mark.parametrize("pattern", ["permut", "desc_ties", "desc_runs"])
+def test_symmetric_full_size(pattern, variant):
+    """gns_sort_symmetric at the benchmark's size (2^27 keys, 50% buffer), on
+    random input and on the inputs whose runs the variants store mirrored:
+    invariants plus sampled positions from the oracle."""
+    need_gpu()
+    import paper_2402_01816_gb300 as g
+    keys = inputs.make_keys(pattern, N_FULL, seed=0)
+    kt = to_dev_keys(keys)
+    pt = to_dev_payload(inputs.index_payload(N_FULL))
+    g.gns_sort_symmetric(kt, pt, variant=g.GECKOSORT1 if variant == "gecko" else g.SQUIDSORT1)
+    assert g.gns_stream_status() == 0
+    k_out = kt.cpu().numpy()
+    p_out = pt.cpu().numpy().view(np.uint32)
+    del kt, pt
+    torch.cuda.empty_cache()
+    check_sorted_stable(keys, k_out, p_out, seed=1)
+
+
 def test_small_config_exact():
     """2^20 uniform[0,1) keys, ascending, 100% buffer: bit-exact against the
     oracle's full stable sort."""
