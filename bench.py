@@ -53,8 +53,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--paper-patterns", action="store_true",
                     help="add the paper's pattern suite on both tiers (ratios in the form of its Squidsort table)")
-    ap.add_argument("--large", action="store_true",
-                    help="add the 2^31-key 50%%-tier run (about 40 GB on the device, minutes of input generation)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 2^31-key low-memory run of the default extras (about 60 GB on the device, 15 s)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the learned-vs-plain and batched-vs-plain comparisons")
     ap.add_argument("--only", default=None,
@@ -783,7 +783,7 @@ def run_ours(args, ws, rank, local):
         extras["learned_network_gain"] = network_gain(dev)
     if args.paper_patterns:
         extras["paper_patterns"] = paper_patterns(dev, args.n)
-    if args.large:
+    if not args.no_extras and not args.no_large and args.n == N_FULL:
         extras["large_low_memory"] = large_low_memory(dev)
     if rank != 0:
         return
