@@ -428,6 +428,25 @@ const char* gns_kernel_name(int kernel_id);
 void gns_set_wait_limit_ns(uint64_t ns);
 void gns_debug_skip_publish(int64_t ticket);
 
+/* Test hook (race detection without a sanitizer): every ticket of the in-place
+ * merge levels and every leaf of their fused setup waits a pseudo-random time
+ * of up to max_ns (at most 50 us; 0 = off, the default) after it is taken and
+ * before it loads its inputs.  Tickets then load in perturbed orders, so a
+ * store that did not wait for every load it overwrites would change the
+ * result; the waits stay far below the wait limit.  Applies to later calls
+ * until reset. */
+void gns_debug_jitter(uint32_t max_ns);
+
+/* Test hook: the merge-path partition of one Nocopy merge level ("Parallel"
+ * section) on its own.  keys: device, n order-mapped 64-bit keys whose
+ * consecutive runs of w keys are sorted (w a multiple of 1024); splits:
+ * device, ceil(n / 2048) int64.  splits[b] receives the number of elements
+ * of the left run among the first b*2048 - p outputs of the stable merge
+ * (left run wins ties) of the pair of runs starting at p = floor(b*2048 /
+ * 2w) * 2w.  Returns GNS_OK, GNS_ERR_INVALID or GNS_ERR_CUDA. */
+int gns_debug_merge_partition(const uint64_t* keys, int64_t n, int64_t w, int64_t* splits,
+                              gns_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

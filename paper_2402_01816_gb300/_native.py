@@ -73,6 +73,8 @@ def lib() -> ctypes.CDLL:
                 "gns_debug_skip_publish": ([i64], None),
                 "gns_learned_half_plan_ok": ([i64], i32),
                 "gns_debug_learned_fault": ([i32], None),
+                "gns_debug_jitter": ([ctypes.c_uint32], None),
+                "gns_debug_merge_partition": ([P, i64, i64, P, P], i32),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -329,3 +331,20 @@ FAULT_NONE, FAULT_BUCKETS_SWAPPED, FAULT_GARBAGE_WEIGHTS, FAULT_SPLITTERS_REVERS
 def gns_debug_learned_fault(kind: int) -> None:
     """Plant one fault into the next gns_learned_sort call (test hook)."""
     lib().gns_debug_learned_fault(int(kind))
+
+
+def gns_debug_jitter(max_ns: int) -> None:
+    """Test hook: perturb the load order of the in-place levels' tickets."""
+    lib().gns_debug_jitter(int(max_ns))
+
+
+def gns_debug_merge_partition(keys, w: int, stream=None):
+    """Test hook: co-ranks of one merge level (keys: CUDA int64 tensor holding
+    order-mapped keys as raw bits); returns a CUDA int64 tensor of splits."""
+    import torch
+    n = keys.numel()
+    splits = torch.empty((n + 2047) // 2048, dtype=torch.int64, device=keys.device)
+    _check(lib().gns_debug_merge_partition(_dev_ptr(keys, torch.int64, "keys"), n, int(w),
+                                           _dev_ptr(splits, torch.int64, "splits"), _stream(stream)),
+           "gns_debug_merge_partition")
+    return splits

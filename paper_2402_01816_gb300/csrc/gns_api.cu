@@ -124,6 +124,8 @@ std::atomic<int64_t> g_debug_skip{-1};
 
 uint64_t wait_limit_ns() { return g_wait_limit_ns.load(); }
 int64_t take_debug_skip_publish() { return g_debug_skip.exchange(-1); }
+std::atomic<uint32_t> g_debug_jitter{0};
+uint32_t debug_jitter_ns() { return g_debug_jitter.load(); }
 
 // ------------------------------------------------------------ profiling
 namespace {
@@ -402,5 +404,6 @@ int gns_release_workspace_cache(void)
 void gns_set_wait_limit_ns(uint64_t ns) { g_wait_limit_ns.store(ns ? ns : 1); }
 
 void gns_debug_skip_publish(int64_t ticket) { g_debug_skip.store(ticket); }
+void gns_debug_jitter(uint32_t max_ns) { g_debug_jitter.store(max_ns > 50000u ? 50000u : max_ns); }
 
 }  // extern "C"

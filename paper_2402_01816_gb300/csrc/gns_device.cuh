@@ -60,6 +60,16 @@ __device__ __forceinline__ int ld_relaxed(const int* p)
     return v;
 }
 
+// Test hook (gns_debug_jitter): a pseudo-random delay of up to max_ns for work
+// item `item` of pass `pass`, so that the in-place passes' tickets load in
+// perturbed orders and a missing dependency wait shows up as a wrong result.
+__device__ __forceinline__ void debug_jitter(uint32_t max_ns, int64_t item, int pass)
+{
+    if (max_ns == 0) return;
+    const uint32_t h = (uint32_t)item * 2654435761u ^ (uint32_t)pass * 40503u;
+    __nanosleep((h ^ (h >> 15)) % max_ns);
+}
+
 __device__ __forceinline__ uint64_t global_ns()
 {
     uint64_t t;

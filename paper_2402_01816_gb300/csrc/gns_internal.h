@@ -76,6 +76,7 @@ void ws_free(void* p, cudaStream_t s);
 // Spin limit of bounded device waits, and the debug fault switch.
 uint64_t wait_limit_ns();
 int64_t take_debug_skip_publish();   // returns the ticket (or -1) and clears it
+uint32_t debug_jitter_ns();           // test hook: bounded random delay before in-place loads (0 = off)
 
 // Folds a call's error word into the per-device status word (one tiny kernel).
 cudaError_t publish_call_error(const int* call_err, cudaStream_t s);

@@ -447,7 +447,7 @@ template <int THREADS, int ITEMS, int VARIANT = FROG_PLAIN>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS)   // <= 64 registers: 1024 threads per SM
     frog_setup_kernel(Slots sl, const FrogNode* __restrict__ leaves, int64_t nleaves, int mode,
                       int* ticket, int* loaded, int* call_err, uint64_t limit_ns,
-                      const int* presorted, int* leaf_ori)
+                      const int* presorted, int* leaf_ori, uint32_t jitter_ns)
 {
     constexpr int T = THREADS * ITEMS;
     if (skip_all(presorted)) return;
@@ -456,7 +456,10 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)   // <= 64 registers:
     __shared__ int64_t s_leaf;
     __shared__ int s_ok;
     const int t = threadIdx.x;
-    if (t == 0) s_leaf = nleaves - 1 - atomicAdd(ticket, 1);
+    if (t == 0) {
+        s_leaf = nleaves - 1 - atomicAdd(ticket, 1);
+        debug_jitter(jitter_ns, s_leaf, 0);               // test hook: the leaf loads late
+    }
     __syncthreads();
     const int64_t leaf = s_leaf;
     const FrogNode x = leaves[leaf];

@@ -433,7 +433,8 @@ __device__ __forceinline__ void ws_shifts(const uint64_t* dk, const uint32_t* dv
 // none left).  FLAGS: publish/await "inputs loaded" flags (in-place level).
 template <int CT, int ITEMS, int S, bool FLAGS, bool SYM, typename Src>
 __device__ __forceinline__ void ws_merge(Src& src, const Slots& sl, bool has_vals, int mode, int* call_err,
-                                         uint64_t limit_ns, int* loaded, int epoch, int64_t skip_ticket)
+                                         uint64_t limit_ns, int* loaded, int epoch, int64_t skip_ticket,
+                                         uint32_t jitter_ns)
 {
     constexpr int C = CT * ITEMS;
     static_assert(S >= 2 && S <= 4, "stages");
@@ -509,6 +510,7 @@ __device__ __forceinline__ void ws_merge(Src& src, const Slots& sl, bool has_val
                             atomicCAS(call_err, 0, GNS_ERR_INTERNAL);
                             na = nb = 0;
                         }
+                        debug_jitter(jitter_ns, L.tk, epoch);  // test hook: the held ticket loads late
                         fence_proxy_async_shared();            // earlier accesses of this stage come first
                         WsInfo inf;
                         inf.g.na = na;
@@ -833,12 +835,12 @@ template <int S, bool SYM = false>
 __global__ void __launch_bounds__(WS_CONSUMERS + 32, ws_frog_ctas_per_sm<S>())
     frog_merge_ws_kernel(Slots sl, const FrogItem* __restrict__ items, int64_t total, int mode, int decode_out,
                          int* ticket, int* loaded, int epoch, int* call_err, uint64_t limit_ns, int64_t skip_ticket,
-                         const int* presorted)
+                         const int* presorted, uint32_t jitter_ns)
 {
     if (skip_all(presorted)) return;
     FrogLevelSrc src{sl, items, total, ticket, decode_out};
     ws_merge<WS_CONSUMERS, WS_ITEMS, S, true, SYM>(src, sl, sl.v0 != nullptr, mode, call_err, limit_ns, loaded,
-                                                   epoch, skip_ticket);
+                                                   epoch, skip_ticket, jitter_ns);
 }
 
 }  // namespace gns

@@ -349,7 +349,7 @@ cudaError_t launch_frog_level_ws(const Slots& sl, const FrogItem* items, int64_t
     const int64_t grid = imin(total, cap);
     return launch(K_FROG_MERGE, frog_merge_ws_kernel<S, SYM>, dim3((unsigned)grid), dim3(WS_CONSUMERS + 32),
                   ws_smem<S>(), s, sl, items, total, mode, decode, ticket, loaded, epoch, call_err, limit,
-                  skip_ticket, skip);
+                  skip_ticket, skip, debug_jitter_ns());
 }
 
 cudaError_t launch_plain_level(const uint64_t* sk, const uint32_t* sv, uint64_t* dk, uint32_t* dv, int64_t n,
@@ -537,7 +537,7 @@ int sort_device_variant(uint64_t* keys, uint32_t* vals, int64_t n, int mode, dou
         const int64_t nleaves = (int64_t)plan.leaves.size();
         GNS_TRY(launch(K_FROG_SETUP, frog_setup_kernel<SORT_THREADS, SORT_ITEMS, FROG_PLAIN>,
                        dim3((unsigned)nleaves), dim3(SORT_THREADS), kSmemTile, s, sl, leaves, nleaves, mode,
-                       tickets + D, flags, call_err, limit, skip, (int*)nullptr));
+                       tickets + D, flags, call_err, limit, skip, (int*)nullptr, debug_jitter_ns()));
         int* lflags = flags + nleaves;
         int64_t skip_ticket = take_debug_skip_publish();
         for (int d = D - 1; d >= 0; --d) {
@@ -576,7 +576,7 @@ int sort_device_variant(uint64_t* keys, uint32_t* vals, int64_t n, int mode, dou
         int* leaf_ori = (int*)(ws + lay.leaf_ori);
         const bool sym = variant != FROG_PLAIN;
         const dim3 sgrid((unsigned)nleaves), sblock(SORT_THREADS);
-#define GNS_SETUP_ARGS sl, leaves, nleaves, mode, tickets + D, flags, call_err, limit, skip, leaf_ori
+#define GNS_SETUP_ARGS sl, leaves, nleaves, mode, tickets + D, flags, call_err, limit, skip, leaf_ori, debug_jitter_ns()
         if (variant == FROG_GECKO)
             GNS_TRY(launch(K_FROG_SETUP, frog_setup_kernel<SORT_THREADS, SORT_ITEMS, FROG_GECKO>, sgrid, sblock,
                            kSmemTile, s, GNS_SETUP_ARGS));
@@ -762,4 +762,20 @@ extern "C" int gns_frog_plan_check(int64_t n, double buffer_fraction)
         level.swap(next);
     }
     return check_leaves(level, n, total);
+}
+
+// Test hook: the merge-path partition of one 100%-tier level on its own
+// (merge_partition_kernel), so that the co-ranks can be checked against their
+// definition.
+extern "C" int gns_debug_merge_partition(const uint64_t* keys, int64_t n, int64_t w, int64_t* splits,
+                                         gns_stream_t stream)
+{
+    using namespace gns;
+    if (n <= 0 || w <= 0 || w % (CHUNK / 2) != 0 || keys == nullptr || splits == nullptr) return GNS_ERR_INVALID;
+    if (((uintptr_t)keys & 7) || ((uintptr_t)splits & 7)) return GNS_ERR_INVALID;
+    const int64_t nblocks = ceil_div(n, CHUNK);
+    cudaStream_t s = (cudaStream_t)stream;
+    const cudaError_t e = launch(K_MERGE_PARTITION, merge_partition_kernel, dim3((unsigned)ceil_div(nblocks, 256)),
+                                 dim3(256), 0, s, keys, n, w, nblocks, splits, (const int*)nullptr);
+    return finish_call(e == cudaSuccess ? GNS_OK : GNS_ERR_CUDA, s);
 }
