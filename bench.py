@@ -62,7 +62,7 @@ def parse_args():
                          "(e.g. permut@100, permut@50), 'segmented' (--nseg segments) or 'learned' "
                          "(the mixture at --n keys, full buffer)")
     ap.add_argument("--variant", default="frog", choices=["frog", "gecko", "squid"],
-                    help="with --only PATTERN@50: the symmetric variant (gns_sort_symmetric)")
+                    help="with --only PATTERN@TIER below 100: the symmetric variant (gns_sort_symmetric)")
     ap.add_argument("--nseg", type=int, default=4096, help="segments for --only segmented")
     return ap.parse_args()
 
@@ -413,7 +413,7 @@ def paper_patterns(dev, n=1 << 27):
     out = {"workload": f"paper patterns, {n} float64 keys + uint32 index payload, 100% and 50% buffer",
            "patterns": {}}
     pay = torch.arange(n, dtype=torch.int64, device=dev).to(torch.int32)
-    tot = {1.0: 0.0, 0.5: 0.0, "squid": 0.0}
+    tot = {1.0: 0.0, 0.5: 0.0, "squid": 0.0, "squid2": 0.0}
     total5 = inputs.PAPER_PATTERNS[:5]       # the TOTAL KPI: permut, tielog2, ascall, asclocal, ascglobal
     for pattern in inputs.PAPER_PATTERNS:
         keys = torch.from_numpy(inputs.make_keys(pattern, n, seed=0)).to(dev)
@@ -437,6 +437,17 @@ def paper_patterns(dev, n=1 << 27):
         row["50%-squidsort1"] = {"ms": t, "gkeys_s": n / t / 1e6, "r_runtime_vs_100": t / row["100%"]["ms"]}
         if pattern in total5:
             tot["squid"] += t
+        # Squidsort2 at p = 1/8: %RAM 1.125, r(%RAM) 0.56 against the 100% tier (the paper's
+        # Squidsort2 row: 0.57)
+        restore()
+        g.gns_sort_symmetric(kt, pt, variant=g.SQUIDSORT1, buffer_fraction=0.125)
+        t = _time_ms(lambda: g.gns_sort_symmetric(kt, pt, variant=g.SQUIDSORT1, buffer_fraction=0.125), restore)
+        ram = 1.0 + g.gns_workspace_bytes(n, 0.125) / (12.0 * n)
+        row["12.5%-squidsort2"] = {"ms": t, "gkeys_s": n / t / 1e6, "pct_ram": ram,
+                                   "r_pct_ram": ram / row["100%"]["pct_ram"], "r_runtime": t / row["100%"]["ms"],
+                                   "r_t_footprint": ram * t / row["100%"]["t_footprint_ms"]}
+        if pattern in total5:
+            tot["squid2"] += t
         if g.gns_stream_status() != 0:
             raise RuntimeError("device status error in paper_patterns")
         a, b = row["100%"], row["50%"]
@@ -450,7 +461,10 @@ def paper_patterns(dev, n=1 << 27):
     out["TOTAL"] = {"ms_100": tot[1.0], "ms_50": tot[0.5], "r_pct_ram": r_ram, "r_runtime": tot[0.5] / tot[1.0],
                     "r_t_footprint": r_ram * tot[0.5] / tot[1.0],
                     "patterns": list(total5), "ms_50_squidsort1": tot["squid"],
-                    "r_runtime_squidsort1": tot["squid"] / tot[1.0]}
+                    "r_runtime_squidsort1": tot["squid"] / tot[1.0],
+                    "ms_12_5_squidsort2": tot["squid2"], "r_runtime_squidsort2": tot["squid2"] / tot[1.0],
+                    "r_pct_ram_squidsort2": (1.0 + g.gns_workspace_bytes(n, 0.125) / (12.0 * n))
+                    / (1.0 + g.gns_workspace_bytes(n, 1.0) / (12.0 * n))}
     return out
 
 
@@ -566,9 +580,9 @@ def run_only(args):
         pay = torch.from_numpy(inputs.index_payload(n).view(np.int32)).to(dev)
         variant = {"frog": g.FROGSORT1, "gecko": g.GECKOSORT1, "squid": g.SQUIDSORT1}[args.variant]
         if args.variant != "frog":
-            if bf != 0.5:
-                raise SystemExit("--variant needs a 50% tier")
-            fn = lambda kt, pt: g.gns_sort_symmetric(kt, pt, variant=variant)   # noqa: E731
+            if bf >= 1.0:
+                raise SystemExit("--variant needs an in-place tier (below 100)")
+            fn = lambda kt, pt: g.gns_sort_symmetric(kt, pt, variant=variant, buffer_fraction=bf)   # noqa: E731
         else:
             fn = lambda kt, pt: g.gns_sort(kt, pt, buffer_fraction=bf)          # noqa: E731
     kt, pt = torch.empty_like(keys), torch.empty_like(pay)

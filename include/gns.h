@@ -111,36 +111,42 @@ int gns_sort_i64(int64_t* keys, uint32_t* payload, int64_t n, int order,
                  double buffer_fraction, gns_stream_t stream);
 
 /*
- * gns_sort_symmetric -- the stable sort of gns_sort at buffer_fraction 1/2 on
- * Frogsort1's layout, in one of the paper's symmetric merging variants:
+ * gns_sort_symmetric -- the stable sort of gns_sort on an in-place tier's
+ * layout (buffer_fraction in [1/64, 1)), in one of the paper's symmetric
+ * merging variants:
  *   GNS_FROGSORT1   every node's run stored in the target order (gns_sort's
- *                   [0.5, 1) tier; "Frogsort1" section): adaptive to
- *                   presorted input only;
+ *                   in-place tiers; "Frogsort1", "Frogsort2" sections):
+ *                   adaptive to presorted input only;
  *   GNS_GECKOSORT1  data-left branches sorted left-ascending and data-right
  *                   branches right-ascending, each merge reading its inner run
  *                   from the far end ("Symmetric merging" section: about 25%
  *                   of the moves saved on ascending and on descending input);
  *   GNS_SQUIDSORT1  the orientation of every run decided by the data
  *                   ("Squidsort" section: Frogsort with Octosort's lazily
- *                   enforced order): a leaf tile whose input is non-increasing
+ *                   enforced order; Squidsort1 on Frogsort1's tree, Squidsort2
+ *                   on Frogsort2's): a leaf tile whose input is non-increasing
  *                   (first key strictly above its last) is stored mirrored, a
  *                   node takes its outer child's orientation, and a mirrored
  *                   root is reversed once at the end, so descending runs --
- *                   ties included -- move only half their elements per level,
- *                   like ascending ones.
- * Every variant returns the same bytes as gns_sort (the unique stable sort);
- * they differ only in how much data moves.  Tiles of up to 8192 elements are
- * the leaves.  As gns_sort, one read pass first detects non-decreasing input
+ *                   ties included -- move only the inner runs' elements per
+ *                   level, like ascending ones.
+ * buffer_fraction selects the tree as gns_sort does: [0.5, 1) Frogsort1's,
+ * [1/64, 0.5) Frogsort2's with inner fraction p = buffer_fraction.  Every
+ * variant returns the same bytes as gns_sort (the unique stable sort); they
+ * differ only in how much data moves.  Tiles of up to 8192 elements are the
+ * leaves.  As gns_sort, one read pass first detects non-decreasing input
  * (nothing to do) and strictly decreasing input (one reversal).
  *
  * Arguments: keys (device, n 64-bit keys of key_type GNS_KEY_F64 or
  * GNS_KEY_I64), payload (device, n uint32, or NULL), n >= 0, order,
- * variant.  Workspace ~ 6 n bytes, as gns_sort at buffer_fraction 1/2.
- * Errors: as gns_sort; GNS_ERR_INVALID for an unknown key type or variant.
+ * buffer_fraction, variant.  Workspace as gns_sort at that buffer_fraction.
+ * Errors: as gns_sort; GNS_ERR_INVALID for an unknown key type or variant;
+ * GNS_ERR_UNSUPPORTED for buffer_fraction >= 1 (no in-place layout) or below
+ * 1/64.
  */
 enum { GNS_FROGSORT1 = 0, GNS_GECKOSORT1 = 1, GNS_SQUIDSORT1 = 2 };
 int gns_sort_symmetric(void* keys, int key_type, uint32_t* payload, int64_t n, int order,
-                       int variant, gns_stream_t stream);
+                       double buffer_fraction, int variant, gns_stream_t stream);
 
 /*
  * gns_sort_host -- the same sort on HOST arrays: copies keys and payload to

@@ -47,7 +47,7 @@ def lib() -> ctypes.CDLL:
             sig = {
                 "gns_sort": ([P, P, i64, i32, f64, P], i32),
                 "gns_sort_i64": ([P, P, i64, i32, f64, P], i32),
-                "gns_sort_symmetric": ([P, i32, P, i64, i32, i32, P], i32),
+                "gns_sort_symmetric": ([P, i32, P, i64, i32, f64, i32, P], i32),
                 "gns_sort_host": ([P, P, i64, i32, i32, f64, P], i32),
                 "gns_sort_noalloc": ([P, P, i64, i32, P], i32),
                 "gns_learned_sort": ([P, P, i64, i32, f64, P, P, P], i32),
@@ -134,9 +134,10 @@ def gns_sort(keys, payload=None, order: int = ASCENDING, buffer_fraction: float 
 
 
 def gns_sort_symmetric(keys, payload=None, order: int = ASCENDING, variant: int = SQUIDSORT1,
-                       stream=None) -> None:
-    """In-place stable sort on Frogsort1's layout (buffer fraction 1/2) in one
-    of the symmetric variants: FROGSORT1, GECKOSORT1 or SQUIDSORT1."""
+                       buffer_fraction: float = 0.5, stream=None) -> None:
+    """In-place stable sort on an in-place tier's layout (Frogsort1's tree for
+    buffer_fraction in [0.5, 1), Frogsort2's below) in one of the symmetric
+    variants: FROGSORT1, GECKOSORT1 or SQUIDSORT1."""
     import torch
     n = keys.numel()
     if payload is not None and payload.numel() != n:
@@ -148,8 +149,8 @@ def gns_sort_symmetric(keys, payload=None, order: int = ASCENDING, variant: int 
     else:
         raise TypeError("keys must be float64 or int64")
     _check(lib().gns_sort_symmetric(_dev_ptr(keys, keys.dtype, "keys"), kt,
-                                    _dev_ptr(payload, torch.int32, "payload"), n, order, int(variant),
-                                    _stream(stream)), "gns_sort_symmetric")
+                                    _dev_ptr(payload, torch.int32, "payload"), n, order,
+                                    float(buffer_fraction), int(variant), _stream(stream)), "gns_sort_symmetric")
 
 
 def gns_sort_host(keys: np.ndarray, payload: np.ndarray | None = None, order: int = ASCENDING,

@@ -268,15 +268,16 @@ int gns_sort_i64(int64_t* keys, uint32_t* payload, int64_t n, int order, double 
     return finish_call(rc, s);
 }
 
-int gns_sort_symmetric(void* keys, int key_type, uint32_t* payload, int64_t n, int order, int variant,
-                       gns_stream_t stream)
+int gns_sort_symmetric(void* keys, int key_type, uint32_t* payload, int64_t n, int order, double buffer_fraction,
+                       int variant, gns_stream_t stream)
 {
     if (key_type != GNS_KEY_F64 && key_type != GNS_KEY_I64) return GNS_ERR_INVALID;
     if (variant != GNS_FROGSORT1 && variant != GNS_GECKOSORT1 && variant != GNS_SQUIDSORT1) return GNS_ERR_INVALID;
-    int rc = check_sort_args(keys, payload, n, order, 0.5);
+    int rc = check_sort_args(keys, payload, n, order, buffer_fraction);   // NaN, negative, < 1/64
     if (rc != GNS_OK) return rc;
+    if (buffer_fraction >= 1.0) return GNS_ERR_UNSUPPORTED;                 // no in-place layout at 100%
     cudaStream_t s = (cudaStream_t)stream;
-    rc = sort_device_variant((uint64_t*)keys, payload, n, mode_of(key_type, order), 0.5, variant, s);
+    rc = sort_device_variant((uint64_t*)keys, payload, n, mode_of(key_type, order), buffer_fraction, variant, s);
     return finish_call(rc, s);
 }
 

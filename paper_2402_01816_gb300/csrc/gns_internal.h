@@ -116,8 +116,8 @@ int num_sms();
 // gns_sort core: keys are raw 64-bit patterns, mode = key type | order bits.
 int sort_device(uint64_t* keys, uint32_t* payload, int64_t n, int mode,
                 double buffer_fraction, cudaStream_t s);
-// sort_device with a symmetric variant of the Frogsort1 tier (bf in [0.5, 1)):
-// 0 = Frogsort1, 1 = Geckosort1, 2 = Squidsort1 (gns_sort_symmetric).
+// sort_device with a symmetric variant of the in-place tiers (bf < 1): 0 =
+// Frogsort, 1 = Geckosort, 2 = Squidsort (gns_sort_symmetric).
 int sort_device_variant(uint64_t* keys, uint32_t* payload, int64_t n, int mode, double buffer_fraction,
                         int variant, cudaStream_t s);
 

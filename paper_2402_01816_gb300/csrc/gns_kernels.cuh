@@ -550,6 +550,16 @@ __device__ __forceinline__ void frog_locate(int64_t idx, const int64_t* __restri
     nchk = cstart[k + 1] - base;
 }
 
+// frog_orient_kernel for a tree planned on the host (Frogsort2): node i of the
+// list takes the orientation of leaf outer_leaf[i], its outermost leaf.
+static __global__ void frog_orient_list_kernel(FrogNode* nodes, int64_t count, const int32_t* __restrict__ outer_leaf,
+                                               const int* __restrict__ leaf_ori, const int* presorted)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count || skip_all(presorted)) return;
+    nodes[i].ori = leaf_ori[outer_leaf[i]];
+}
+
 // splits[base(k) + c] = co-rank (left-run elements) of output c*CHUNK of node k.
 //
 // SYM (nodes of either orientation): the merge runs in slot order.  An

@@ -85,6 +85,10 @@ void frog2_split(const FrogNode& p, int64_t pn, FrogNode& L, FrogNode& R)
 struct Frog2Plan {
     std::vector<FrogNode> internal, children, leaves;
     std::vector<int64_t> cstart, first_node, first_cs;
+    // index into `leaves` of the outermost leaf of internal[i] (i < #internal)
+    // and of children[j] (at #internal + j): a node of a symmetric variant
+    // takes that leaf's orientation (frog_orient_kernel)
+    std::vector<int32_t> outer_leaf;
     int64_t max_items = 0;
     int D = 0;
 };
@@ -123,6 +127,19 @@ Frog2Plan frog2_plan(int64_t n, int64_t pn)
     }
     P.first_node.push_back((int64_t)P.internal.size());
     std::sort(P.leaves.begin(), P.leaves.end(), [](const FrogNode& a, const FrogNode& b) { return a.s < b.s; });
+    // outermost leaf: a data-left node's leftmost leaf (the one starting at its
+    // first element), a data-right node's rightmost (the one holding its last)
+    auto leaf_at = [&](int64_t pos) {
+        int64_t lo = 0, hi = (int64_t)P.leaves.size() - 1;    // last leaf with s <= pos
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (P.leaves[mid].s <= pos) lo = mid;
+            else hi = mid - 1;
+        }
+        return (int32_t)lo;
+    };
+    for (const std::vector<FrogNode>* v : {&P.internal, &P.children})
+        for (const FrogNode& x : *v) P.outer_leaf.push_back(leaf_at(x.side == 0 ? x.s : x.s + x.n - 1));
     return P;
 }
 
@@ -134,8 +151,8 @@ struct Frog2Dev {
     int dev = -1;
     int64_t n = 0, pn = 0;
     Frog2Plan plan;               // host copy: per-depth offsets and totals
-    char* d = nullptr;            // internal | children | leaves | cstart
-    size_t o_ch = 0, o_lv = 0, o_cs = 0;
+    char* d = nullptr;            // internal | children | leaves | cstart | outer_leaf
+    size_t o_ch = 0, o_lv = 0, o_cs = 0, o_ol = 0;
     uint64_t used = 0;
 };
 std::mutex g_frog2_mu;
@@ -161,12 +178,14 @@ const Frog2Dev* frog2_get(int64_t n, int64_t pn)
     e.o_ch = P.internal.size() * sizeof(FrogNode);
     e.o_lv = e.o_ch + P.children.size() * sizeof(FrogNode);
     e.o_cs = e.o_lv + P.leaves.size() * sizeof(FrogNode);
-    const size_t bytes = e.o_cs + P.cstart.size() * sizeof(int64_t);
+    e.o_ol = e.o_cs + P.cstart.size() * sizeof(int64_t);
+    const size_t bytes = e.o_ol + P.outer_leaf.size() * sizeof(int32_t);
     std::vector<char> blob(bytes);
     if (!P.internal.empty()) memcpy(blob.data(), P.internal.data(), e.o_ch);
     if (!P.children.empty()) memcpy(blob.data() + e.o_ch, P.children.data(), e.o_lv - e.o_ch);
     if (!P.leaves.empty()) memcpy(blob.data() + e.o_lv, P.leaves.data(), e.o_cs - e.o_lv);
-    if (!P.cstart.empty()) memcpy(blob.data() + e.o_cs, P.cstart.data(), bytes - e.o_cs);
+    if (!P.cstart.empty()) memcpy(blob.data() + e.o_cs, P.cstart.data(), e.o_ol - e.o_cs);
+    if (!P.outer_leaf.empty()) memcpy(blob.data() + e.o_ol, P.outer_leaf.data(), bytes - e.o_ol);
     if (cudaMalloc(&e.d, bytes ? bytes : 16) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
@@ -198,7 +217,8 @@ struct Layout {
     int L, D;
 };
 
-Layout make_layout(int64_t n, double bf, bool with_vals, const Frog2Plan* plan)
+// sym: a symmetric variant (per-call copies of a host-planned tree's nodes).
+Layout make_layout(int64_t n, double bf, bool with_vals, const Frog2Plan* plan, bool sym = false)
 {
     Layout o{};
     size_t off = 0;
@@ -214,6 +234,12 @@ Layout make_layout(int64_t n, double bf, bool with_vals, const Frog2Plan* plan)
         o.flags = off; o.flags_bytes = align256((plan->leaves.size() + (size_t)plan->max_items) * 4);
         off += o.flags_bytes;
         o.tickets = off; o.tickets_bytes = align256((size_t)(plan->D + 2) * 4); off += o.tickets_bytes;
+        if (sym) {
+            // the leaves' orientations and a copy of the internal and child
+            // nodes, whose orientations are set per call
+            o.leaf_ori = off; off += align256(plan->leaves.size() * 4);
+            o.nodes = off; off += align256((plan->internal.size() + plan->children.size()) * sizeof(FrogNode));
+        }
     } else if (bf >= 1.0) {
         o.L = merge_levels(n);
         int64_t nblocks = ceil_div(n, CHUNK);
@@ -480,8 +506,9 @@ done:
     return rc;
 }
 
-// variant (Frogsort1's tree only, bf in [0.5, 1)): FROG_PLAIN = Frogsort1,
-// FROG_GECKO = Geckosort1, FROG_SQUID = Squidsort1 (frog_setup_kernel).
+// variant (the in-place tiers, bf < 1): FROG_PLAIN = Frogsort1/2, FROG_GECKO =
+// Geckosort, FROG_SQUID = Squidsort (frog_setup_kernel), on Frogsort1's tree
+// for bf in [0.5, 1) and on Frogsort2's below.
 int sort_device_variant(uint64_t* keys, uint32_t* vals, int64_t n, int mode, double bf, int variant,
                         cudaStream_t s)
 {
@@ -505,7 +532,7 @@ int sort_device_variant(uint64_t* keys, uint32_t* vals, int64_t n, int mode, dou
         fp = frog2_get(n, frog2_num(bf));
         if (!fp) return GNS_ERR_CUDA;
     }
-    const Layout lay = make_layout(n, bf, vals != nullptr, frog2 ? &fp->plan : nullptr);
+    const Layout lay = make_layout(n, bf, vals != nullptr, frog2 ? &fp->plan : nullptr, variant != FROG_PLAIN);
     char* ws = (char*)ws_alloc(lay.total, s);
     if (!ws) return GNS_ERR_OOM;
     init_attributes();
@@ -524,8 +551,15 @@ int sort_device_variant(uint64_t* keys, uint32_t* vals, int64_t n, int mode, dou
         sl.k1 = (uint64_t*)(ws + lay.bufk);
         sl.v1 = vals ? (uint32_t*)(ws + lay.bufv) : nullptr;
         const Frog2Plan& plan = fp->plan;
-        const FrogNode* internal = (const FrogNode*)fp->d;
-        const FrogNode* children = (const FrogNode*)(fp->d + fp->o_ch);
+        const bool sym = variant != FROG_PLAIN;
+        // symmetric variants: the node lists are copied per call, since the
+        // data sets their orientations (the cached plan is shared)
+        const int64_t nlist = (int64_t)(plan.internal.size() + plan.children.size());
+        FrogNode* nodes2 = (FrogNode*)(ws + lay.nodes);
+        int* leaf_ori = (int*)(ws + lay.leaf_ori);
+        if (sym) GNS_TRY(cudaMemcpyAsync(nodes2, fp->d, (size_t)nlist * sizeof(FrogNode), cudaMemcpyDeviceToDevice, s));
+        const FrogNode* internal = sym ? nodes2 : (const FrogNode*)fp->d;
+        const FrogNode* children = sym ? nodes2 + plan.internal.size() : (const FrogNode*)(fp->d + fp->o_ch);
         const FrogNode* leaves = (const FrogNode*)(fp->d + fp->o_lv);
         const int64_t* cstart = (const int64_t*)(fp->d + fp->o_cs);
         int64_t* splits = (int64_t*)(ws + lay.splits);
@@ -535,9 +569,21 @@ int sort_device_variant(uint64_t* keys, uint32_t* vals, int64_t n, int mode, dou
         const uint64_t limit = wait_limit_ns();
         GNS_TRY(cudaMemsetAsync(flags, 0, lay.flags_bytes + lay.tickets_bytes, s));
         const int64_t nleaves = (int64_t)plan.leaves.size();
-        GNS_TRY(launch(K_FROG_SETUP, frog_setup_kernel<SORT_THREADS, SORT_ITEMS, FROG_PLAIN>,
-                       dim3((unsigned)nleaves), dim3(SORT_THREADS), kSmemTile, s, sl, leaves, nleaves, mode,
-                       tickets + D, flags, call_err, limit, skip, (int*)nullptr, debug_jitter_ns()));
+        const dim3 sgrid((unsigned)nleaves), sblock(SORT_THREADS);
+#define GNS_SETUP2_ARGS sl, leaves, nleaves, mode, tickets + D, flags, call_err, limit, skip, leaf_ori, debug_jitter_ns()
+        if (variant == FROG_GECKO)
+            GNS_TRY(launch(K_FROG_SETUP, frog_setup_kernel<SORT_THREADS, SORT_ITEMS, FROG_GECKO>, sgrid, sblock,
+                           kSmemTile, s, GNS_SETUP2_ARGS));
+        else if (variant == FROG_SQUID)
+            GNS_TRY(launch(K_FROG_SETUP, frog_setup_kernel<SORT_THREADS, SORT_ITEMS, FROG_SQUID>, sgrid, sblock,
+                           kSmemTile, s, GNS_SETUP2_ARGS));
+        else
+            GNS_TRY(launch(K_FROG_SETUP, frog_setup_kernel<SORT_THREADS, SORT_ITEMS, FROG_PLAIN>, sgrid, sblock,
+                           kSmemTile, s, GNS_SETUP2_ARGS));
+#undef GNS_SETUP2_ARGS
+        if (sym && nlist > 0)
+            GNS_TRY(launch(K_FROG_PLAN, frog_orient_list_kernel, dim3((unsigned)ceil_div(nlist, 256)), dim3(256), 0, s,
+                           nodes2, nlist, (const int32_t*)(fp->d + fp->o_ol), (const int*)leaf_ori, skip));
         int* lflags = flags + nleaves;
         int64_t skip_ticket = take_debug_skip_publish();
         for (int d = D - 1; d >= 0; --d) {
@@ -546,15 +592,27 @@ int sort_device_variant(uint64_t* keys, uint32_t* vals, int64_t n, int mode, dou
             const FrogNode* level = internal + f0;
             const FrogNode* child = children + 2 * f0;
             const int64_t* cs = cstart + c0;
-            GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel<false>, dim3((unsigned)ceil_div(total, 256)), dim3(256), 0,
-                           s, sl, level, child, nnodes, (int64_t)0, cs, total, splits, skip));
-            GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel<false>, dim3((unsigned)ceil_div(total, 256)), dim3(256), 0, s,
-                           level, child, nnodes, (int64_t)0, cs, total, (const int64_t*)splits, items, call_err,
-                           skip, (int)(d != 0)));
+            const dim3 pgrid((unsigned)ceil_div(total, 256));
+            if (sym) {
+                GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel<true>, pgrid, dim3(256), 0, s, sl, level,
+                               child, nnodes, (int64_t)0, cs, total, splits, skip));
+                GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel<true>, pgrid, dim3(256), 0, s, level, child,
+                               nnodes, (int64_t)0, cs, total, (const int64_t*)splits, items, call_err, skip,
+                               (int)(d != 0)));
+            } else {
+                GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel<false>, pgrid, dim3(256), 0, s, sl, level,
+                               child, nnodes, (int64_t)0, cs, total, splits, skip));
+                GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel<false>, pgrid, dim3(256), 0, s, level, child,
+                               nnodes, (int64_t)0, cs, total, (const int64_t*)splits, items, call_err, skip,
+                               (int)(d != 0)));
+            }
             GNS_TRY(launch_frog_level(sl, (const FrogItem*)items, total, mode, (int)(d == 0), tickets + d, lflags,
-                                      D - d, call_err, limit, skip_ticket, skip, s));
+                                      D - d, call_err, limit, skip_ticket, skip, s, sym));
             skip_ticket = -1;
         }
+        if (variant == FROG_SQUID && !plan.internal.empty())   // a mirrored root: the one final reversal
+            GNS_TRY(launch(K_REVERSE, reverse_root_kernel, dim3((unsigned)(num_sms() * 8)), dim3(256), 0, s, keys,
+                           vals, n, internal, (const int*)ctl));
     } else {
         const int D = lay.D;
         Slots sl;

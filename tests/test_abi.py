@@ -196,20 +196,24 @@ def test_learned_host_argument_checks(L, args):
     assert L.gns_learned_sort(k, p, n, order, bf, None, None, None) == -1
 
 
-@pytest.mark.parametrize("args", [
-    (FAKE, 0, None, 10, 0, 3),                 # unknown variant
-    (FAKE, 0, None, 10, 0, -1),
-    (FAKE, 2, None, 10, 0, 1),                 # unknown key type
-    (FAKE, 0, None, -1, 0, 1),                 # n < 0
-    (None, 0, None, 10, 0, 2),                 # NULL keys with n > 0
-    (FAKE, 0, None, 10, 2, 2),                 # unknown order
-    (FAKE + 4, 0, None, 10, 0, 1),             # keys not 8-byte aligned
-    (FAKE, 1, FAKE + 40, 10, 0, 2),            # keys and payload overlap
+@pytest.mark.parametrize("args,code", [
+    ((FAKE, 0, None, 10, 0, 0.5, 3), -1),                 # unknown variant
+    ((FAKE, 0, None, 10, 0, 0.5, -1), -1),
+    ((FAKE, 2, None, 10, 0, 0.5, 1), -1),                 # unknown key type
+    ((FAKE, 0, None, -1, 0, 0.5, 1), -1),                 # n < 0
+    ((None, 0, None, 10, 0, 0.5, 2), -1),                 # NULL keys with n > 0
+    ((FAKE, 0, None, 10, 2, 0.5, 2), -1),                 # unknown order
+    ((FAKE + 4, 0, None, 10, 0, 0.5, 1), -1),             # keys not 8-byte aligned
+    ((FAKE, 1, FAKE + 40, 10, 0, 0.5, 2), -1),            # keys and payload overlap
+    ((FAKE, 0, None, 10, 0, math.nan, 2), -1),            # NaN buffer fraction
+    ((FAKE, 0, None, 10, 0, -0.5, 2), -1),                # negative buffer fraction
+    ((FAKE, 0, None, 10, 0, 1.0, 2), -2),                 # no in-place layout at 100%
+    ((FAKE, 0, None, 10, 0, 0.01, 1), -2),                # below the smallest Frogsort2 inner fraction
 ])
-def test_symmetric_host_argument_checks(L, args):
-    assert L.gns_sort_symmetric(*args, None) == -1
+def test_symmetric_host_argument_checks(L, args, code):
+    assert L.gns_sort_symmetric(*args, None) == code
 
 
 def test_symmetric_trivial_sizes_are_no_ops(L):
-    assert L.gns_sort_symmetric(None, 0, None, 0, 0, 2, None) == 0
-    assert L.gns_sort_symmetric(FAKE, 1, None, 1, 1, 1, None) == 0
+    assert L.gns_sort_symmetric(None, 0, None, 0, 0, 0.5, 2, None) == 0
+    assert L.gns_sort_symmetric(FAKE, 1, None, 1, 1, 0.25, 1, None) == 0

@@ -38,7 +38,7 @@ def _sort_and_check(keys, order, fn):
 
 
 @pytest.mark.parametrize("pattern", ["permut", "asc_noise", "desc_ties", "ties", "desc_runs"])
-@pytest.mark.parametrize("form", ["frog1", "frog2", "gecko", "squid"])
+@pytest.mark.parametrize("form", ["frog1", "frog2", "gecko", "squid", "squid2"])
 def test_in_place_tiers_under_jitter(form, pattern):
     need_gpu()
     import paper_2402_01816_gb300 as g
@@ -50,6 +50,8 @@ def test_in_place_tiers_under_jitter(form, pattern):
             g.gns_sort(kt, pt, order=order, buffer_fraction=0.5)
         elif form == "frog2":
             g.gns_sort(kt, pt, order=order, buffer_fraction=0.25)
+        elif form == "squid2":
+            g.gns_sort_symmetric(kt, pt, order=order, variant=g.SQUIDSORT1, buffer_fraction=0.25)
         else:
             g.gns_sort_symmetric(kt, pt, order=order, variant=g.GECKOSORT1 if form == "gecko" else g.SQUIDSORT1)
     g.gns_debug_jitter(20000)

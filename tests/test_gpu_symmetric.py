@@ -19,13 +19,13 @@ SIZES = [0, 1, 2, 3, 255, 2 * TILE - 1, 2 * TILE, 2 * TILE + 1, 3 * TILE + 5, 4 
 VARIANTS = {"gecko": 1, "squid": 2, "frog": 0}
 
 
-def _run(keys, order, variant, with_payload=True):
+def _run(keys, order, variant, with_payload=True, bf=0.5):
     import paper_2402_01816_gb300 as g
     n = keys.size
     pay = inputs.index_payload(n)
     kt = to_dev_keys(keys)
     pt = to_dev_payload(pay) if with_payload else None
-    g.gns_sort_symmetric(kt, pt, order=order, variant=variant)
+    g.gns_sort_symmetric(kt, pt, order=order, variant=variant, buffer_fraction=bf)
     assert g.gns_stream_status() == 0
     got_k, got_p = from_dev(kt, pt)
     want_k, want_p = oracle.stable_sort(keys, pay if with_payload else None,
@@ -123,3 +123,27 @@ def test_offset_views():
     got_k, got_p = from_dev(kt, pt)
     assert_bitexact(got_k, got_p, want_k, want_p)
     assert big_k[:3].abs().sum().item() == 0 and big_p[0].item() == 0 and big_p[n + 1:].abs().sum().item() == 0
+
+
+@pytest.mark.parametrize("bf", [0.4, 0.25, 0.1])
+@pytest.mark.parametrize("variant", ["gecko", "squid"])
+@pytest.mark.parametrize("pattern", ["permut", "ties", "asc_noise", "desc_ties", "desc_runs", "descall", "uniform"])
+def test_frogsort2_tree(pattern, variant, bf):
+    """Geckosort and Squidsort on Frogsort2's imbalanced tree (Squidsort2 in the
+    paper's table): node lists planned on the host, orientations set per call."""
+    need_gpu()
+    n = 70 * TILE + 1234
+    order = 1 if pattern == "ties" else 0
+    _run(inputs.make_keys(pattern, n, seed=13), order, VARIANTS[variant], bf=bf)
+
+
+@pytest.mark.parametrize("variant", ["gecko", "squid"])
+def test_frogsort2_tree_sizes_and_edges(variant):
+    need_gpu()
+    rng = np.random.default_rng(29)
+    v = VARIANTS[variant]
+    for n in (2 * TILE + 1, 5 * TILE + 3, 33 * TILE + 77, (1 << 20) + 12345):
+        _run(inputs.make_keys("desc_noise", n, seed=n), n % 2, v, bf=0.25)
+    alpha = inputs.edge_alphabet()
+    _run(alpha[rng.integers(0, alpha.size, 9 * TILE + 1)], 1, v, bf=0.2)
+    _run(rng.integers(-2**63, 2**63 - 1, 9 * TILE + 1, dtype=np.int64, endpoint=True), 0, v, bf=0.2, with_payload=False)
