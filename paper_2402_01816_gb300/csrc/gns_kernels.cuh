@@ -39,9 +39,17 @@ constexpr int TILE = SORT_THREADS * SORT_ITEMS;       // elements per tile (8192
 #define GNS_MERGE_CONSUMERS 256
 #endif
 constexpr int MERGE_CONSUMERS = GNS_MERGE_CONSUMERS;
-constexpr int MERGE_ITEMS = 8;
-constexpr int CHUNK = MERGE_CONSUMERS * MERGE_ITEMS;  // outputs per merge chunk
-static_assert(CHUNK == 1024 || CHUNK == 2048, "merge chunk size");
+#ifndef GNS_MERGE_ITEMS
+#define GNS_MERGE_ITEMS 9
+#endif
+// 9 outputs per consumer thread: neighbouring lanes' run heads then lie 9
+// elements (18 words) apart where a thread's outputs come from one run, and
+// 4.5 apart where they alternate -- distinct banks either way.  With 8 (a
+// 16-word stride) every lane's block starts at word 0 or 16 modulo 32 and
+// such reads conflict 8-fold.  The last consumers of a chunk have nothing to do.
+constexpr int MERGE_ITEMS = GNS_MERGE_ITEMS;
+constexpr int CHUNK = MERGE_CONSUMERS == 128 ? 1024 : 2048;   // outputs per merge chunk
+static_assert(MERGE_CONSUMERS * MERGE_ITEMS >= CHUNK, "merge chunk size");
 constexpr int DETECT_TILE = 4096;
 
 // Shared-memory index with one pad slot per 16 elements: thread t's blocked

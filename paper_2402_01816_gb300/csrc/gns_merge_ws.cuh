@@ -14,7 +14,7 @@
 //   * reuses a stage once its store has read it.
 // The consumers merge: wait for a stage (in the in-place level the first
 // consumer thread then publishes the item's "inputs loaded" flag), split it by
-// merge path (8 outputs per thread), merge serially in registers, and -- after
+// merge path (MERGE_ITEMS = 9 outputs per thread), merge serially in registers, and -- after
 // a barrier, since the stage is their input -- write the outputs back into the
 // same stage,
 // placed so that shared and global addresses agree modulo 16 bytes (one bulk
@@ -36,8 +36,8 @@ namespace gns {
 
 constexpr int WS_CONSUMERS = MERGE_CONSUMERS;
 constexpr int WS_ITEMS = MERGE_ITEMS;
-constexpr int WS_CHUNK = WS_CONSUMERS * WS_ITEMS;   // outputs per item
-static_assert(WS_CHUNK == CHUNK, "merge chunk size");
+constexpr int WS_CHUNK = CHUNK;                     // outputs per item (the stages hold one)
+static_assert(WS_CONSUMERS * WS_ITEMS >= WS_CHUNK, "merge chunk size");
 
 // Resident CTAs per SM the S-stage layouts are sized for (shared memory and
 // registers): six 160-thread CTAs with 1024-output stages, three 288-thread
@@ -173,7 +173,7 @@ __device__ __forceinline__ unsigned stage_slice_1t(uint64_t* sk, uint32_t* svv, 
     return bytes;
 }
 
-// Merge of a staged chunk by consumer thread `ct`: its outputs [8 ct, 8 ct + 8).
+// Merge of a staged chunk by consumer thread `ct`: its outputs [ITEMS ct, ITEMS ct + ITEMS).
 template <int C, int ITEMS>
 __device__ __forceinline__ int merge_staged_ct(const InStage<C>& st, const StagedChunk& g, uint64_t (&k)[ITEMS],
                                                uint32_t (&v)[ITEMS], bool has_vals, int ct)
@@ -333,14 +333,15 @@ __device__ __forceinline__ void rotate_left(T (&a)[N], int r)
     }
 }
 
-// Thread ct's m outputs to keys ok[shk + 8 ct ...] and payload ov[shv + 8 ct ...].
-// A full set of outputs is written one element per store in a rotated order:
-// at step y thread ct writes its element (y + r) mod 8, r = ct / 2 for keys
-// and ct / 4 for the payload.  Within a half-warp (8-byte keys) the 16
-// threads' slots ((8 ct + element) mod 16) are then all different, and so are
-// the 32 threads' payload banks ((8 ct + element) mod 32), whatever the shift:
-// no bank conflicts.  (Stores of a thread's 8 consecutive elements in element
-// order put every thread of a quarter- or half-warp on the same few banks.)
+// Thread ct's m outputs to keys ok[shk + ITEMS ct ...] and payload
+// ov[shv + ITEMS ct ...].  With an odd ITEMS the threads' blocks start an odd
+// number of payload words (and twice that many key words) apart, so a store
+// step of all threads hits distinct banks as it is.  With ITEMS = 8 a full set
+// of outputs is written one element per store in a rotated order: at step y
+// thread ct writes its element (y + r) mod 8, r = ct / 2 for keys and ct / 4
+// for the payload, so that within a half-warp (8-byte keys) the 16 threads'
+// slots ((8 ct + element) mod 16) are all different, and so are the 32
+// threads' payload banks ((8 ct + element) mod 32), whatever the shift.
 template <int ITEMS>
 __device__ __forceinline__ void write_out_shifted(uint64_t* ok, uint32_t* ov, int shk, int shv,
                                                   uint64_t (&kk)[ITEMS], uint32_t (&v)[ITEMS], int m,
@@ -352,18 +353,28 @@ __device__ __forceinline__ void write_out_shifted(uint64_t* ok, uint32_t* ov, in
         for (int x = 0; x < ITEMS; ++x) kk[x] = decode_key(kk[x], mode);
     }
     if (m == ITEMS) {
-        static_assert(ITEMS == 8, "rotated write-out assumes 8 outputs per thread");
-        uint64_t* dk = ok + shk + diag;
-        const int rk = (ct >> 1) & 7;
-        rotate_left<ITEMS>(kk, rk);
+        if constexpr ((ITEMS & 1) != 0) {
+            // an odd count: thread blocks start 2*ITEMS words apart (keys) and
+            // ITEMS words apart (payload), distinct banks with no rotation
 #pragma unroll
-        for (int y = 0; y < ITEMS; ++y) dk[(y + rk) & 7] = kk[y];
-        if (has_vals) {
-            uint32_t* dv = ov + shv + diag;
-            const int rv = (ct >> 2) & 7;
-            rotate_left<ITEMS>(v, rv);
+            for (int y = 0; y < ITEMS; ++y) {
+                ok[shk + diag + y] = kk[y];
+                if (has_vals) ov[shv + diag + y] = v[y];
+            }
+        } else {
+            static_assert(ITEMS == 8, "rotated write-out assumes 8 outputs per thread");
+            uint64_t* dk = ok + shk + diag;
+            const int rk = (ct >> 1) & 7;
+            rotate_left<ITEMS>(kk, rk);
 #pragma unroll
-            for (int y = 0; y < ITEMS; ++y) dv[(y + rv) & 7] = v[y];
+            for (int y = 0; y < ITEMS; ++y) dk[(y + rk) & 7] = kk[y];
+            if (has_vals) {
+                uint32_t* dv = ov + shv + diag;
+                const int rv = (ct >> 2) & 7;
+                rotate_left<ITEMS>(v, rv);
+#pragma unroll
+                for (int y = 0; y < ITEMS; ++y) dv[(y + rv) & 7] = v[y];
+            }
         }
     } else {
 #pragma unroll
@@ -436,8 +447,8 @@ __device__ __forceinline__ void ws_merge(Src& src, const Slots& sl, bool has_val
                                          uint64_t limit_ns, int* loaded, int epoch, int64_t skip_ticket,
                                          uint32_t jitter_ns)
 {
-    constexpr int C = CT * ITEMS;
-    static_assert(S >= 2 && S <= 4, "stages");
+    constexpr int C = WS_CHUNK;
+    static_assert(S >= 2 && S <= 4 && CT * ITEMS >= C, "stages");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     WsSmem<C, S>& sm = *reinterpret_cast<WsSmem<C, S>*>(smem_raw);
     __shared__ __align__(8) uint64_t full[S];
@@ -622,7 +633,8 @@ struct WsSmemOut {
 template <int CT, int ITEMS, int S, typename Src>
 __device__ __forceinline__ void ws_merge_out(Src& src, bool has_vals, int mode, int* call_err, uint64_t limit_ns)
 {
-    constexpr int C = CT * ITEMS;
+    constexpr int C = WS_CHUNK;
+    static_assert(CT * ITEMS >= C, "consumers cover a chunk");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     WsSmemOut<C, S>& sm = *reinterpret_cast<WsSmemOut<C, S>*>(smem_raw);
     __shared__ __align__(8) uint64_t full[S];
