@@ -38,7 +38,10 @@ constexpr int SAMPLE_M = 1 << 16;     // sample size (power of two)
 constexpr int GRID_G = 1 << 16;       // grid for inverting the fitted CDF
 constexpr int NBUCKETS = 4096;
 constexpr int NSPLIT = NBUCKETS - 1;
-constexpr int TABLE_BITS = 22;        // bins of the key -> bucket-range table (global, L2-resident)
+constexpr int TABLE_BITS = 22;        // about 2^22 fine bins of the key -> bucket-range table (global, L2-resident)
+constexpr int COARSE_BITS = 10;       // coarse bins, uniform in the prefix space, that share the fine bins out
+constexpr int NCOARSE = 1 << COARSE_BITS;
+constexpr int64_t TABLE_MAX = (1ll << TABLE_BITS) + NCOARSE;   // fine bins at most
 constexpr int PART_TILE = 2048;       // keys per partition tile
 constexpr int PART_THREADS = 256;
 constexpr int PART_ITEMS = PART_TILE / PART_THREADS;
@@ -280,8 +283,10 @@ constexpr int NKNOTS = 64;            // first stage: 64 intervals between sampl
 struct LearnMeta {
     uint64_t lo53;        // 53-bit prefix of the smallest sample key
     uint64_t range;       // prefix of the largest minus lo53 (>= 1)
-    int sh;               // table bin = (prefix - lo53) >> sh
+    int sh;               // coarse bin = (prefix - lo53) >> sh, below NCOARSE
     int bad;              // splitters not non-decreasing (never expected)
+    int nfine;            // fine bins of the table (entries nfine + 1)
+    int nuniq;            // distinct splitter values
     int64_t max_bucket;
     int nonempty, overfull, tied;
     int verify_failed;    // the bucket check failed: the plain sort re-sorts the array
@@ -343,7 +348,7 @@ __global__ void fit_meta_kernel(const uint64_t* __restrict__ sample, int mode, L
         meta->lo53 = lo;
         meta->range = range;
         int sh = 0;
-        while ((range >> sh) >= (1ull << TABLE_BITS)) ++sh;
+        while ((range >> sh) >= (uint64_t)NCOARSE) ++sh;
         meta->sh = sh;
         meta->bad = 0;
         meta->verify_failed = 0;
@@ -425,17 +430,6 @@ __global__ void splitter_kernel(const float* __restrict__ F, LearnMeta* meta, ui
     spl[j - 1] = first_stage_inverse(meta, (double)lo / (double)(GRID_G - 1));
 }
 
-__device__ __forceinline__ int count_le(const uint64_t* spl, uint64_t e53)
-{
-    int lo = 0, hi = NSPLIT;                      // number of splitters <= e53
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (spl[mid] <= e53) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
 // Splitter post-processing: a run of equal splitters marks a point mass (many
 // keys with one prefix); the splitter after the run is moved down to the
 // mass's prefix + 1, so that the mass has a bucket of its own (one prefix
@@ -451,82 +445,237 @@ __global__ void isolate_masses_kernel(const uint64_t* __restrict__ spl_in, uint6
     if (j > 0 && spl_in[j] < spl_in[j - 1]) atomicExch(&meta->bad, 1);
 }
 
-// T[b] = bucket of prefix lo53 + (b << sh), for b = 0 .. 2^22 (the bucket of
-// every key in bin b lies in [T[b], T[b+1]]).  The table is read through L2 by
-// every key; with 2^22 bins over the sample's range it resolves almost every
-// key to one bucket.
-__global__ void __launch_bounds__(256) table_kernel(const uint64_t* __restrict__ spl, const LearnMeta* __restrict__ meta,
-                                                    uint16_t* __restrict__ table)
+// The key -> bucket-range table.  A key's bucket is the number of splitters
+// at or below its prefix.  Keys are located in two steps, both monotone in the
+// prefix:
+//   coarse bin  c = (prefix - lo53) >> sh, one of NCOARSE uniform bins of the
+//               sample's range;
+//   fine bin    coarse bin c owns fine bins [off_c, off_c + 2^(sh - s_c)) and
+//               the prefix falls into off_c + ((prefix - lo53) mod 2^sh) >> s_c.
+// Each coarse bin gets fine bins in proportion to the sample keys it holds (a
+// power of two, at least one, at most one per prefix), so that the ~2^22 fine
+// bins follow the data rather than the width of the key space (the range of
+// float keys spans every exponent between the smallest and the largest).
+// coarse[c] packs off_c (low 26 bits) and s_c (high 6 bits).
+__device__ __forceinline__ int64_t fine_bin(const uint32_t* coarse, uint64_t d, int sh)
 {
-    __shared__ uint64_t s_spl[NSPLIT];
-    for (int i = threadIdx.x; i < NSPLIT; i += blockDim.x) s_spl[i] = spl[i];
+    const uint32_t cw = coarse[d >> sh];
+    const uint64_t r = d & ((1ull << sh) - 1ull);
+    return (int64_t)(cw & 0x3ffffffu) + (int64_t)(r >> (cw >> 26));
+}
+
+// Fine-bin shares of the coarse bins from the sorted sample (one CTA of
+// NCOARSE threads); writes coarse[] and meta->nfine.
+__global__ void __launch_bounds__(NCOARSE) coarse_kernel(const uint64_t* __restrict__ sample, int mode,
+                                                         LearnMeta* meta, uint32_t* __restrict__ coarse)
+{
+    __shared__ uint32_t cnt[NCOARSE];
+    __shared__ uint32_t wsum[NCOARSE / 32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    cnt[t] = 0;
+    __syncthreads();
+    const uint64_t lo53 = meta->lo53;
+    const int sh = meta->sh;
+    for (int i = t; i < SAMPLE_M; i += NCOARSE) atomicAdd(&cnt[((encode_key(sample[i], mode) >> 11) - lo53) >> sh], 1u);
+    __syncthreads();
+    // share: the largest power of two at most cnt * 2^TABLE_BITS / SAMPLE_M,
+    // at least 1, at most 2^sh (one fine bin per prefix)
+    const uint64_t want = (uint64_t)cnt[t] << TABLE_BITS >> 16;
+    static_assert(SAMPLE_M == 1 << 16, "fine-bin share");
+    int lg = want > 0 ? 63 - __clzll((long long)want) : 0;
+    lg = lg < sh ? lg : sh;
+    const uint32_t alloc = 1u << lg;
+    uint32_t x = alloc;                                   // exclusive scan of the shares
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = wsum[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, w, d);
+            if (lane >= d) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t off = x - alloc + (wid > 0 ? wsum[wid - 1] : 0u);
+    coarse[t] = off | ((uint32_t)(sh - lg) << 26);
+    if (t == NCOARSE - 1) meta->nfine = (int)(off + alloc);
+}
+
+// The distinct splitter values (uniq[0 .. m)) and, for each, the number of
+// splitters below it (cum[k] = index of its first splitter; cum[m] = NSPLIT):
+// the bucket of a key is cum[#distinct values at or below its prefix].  A run
+// of equal splitters (a point mass of the sample) is then one entry, not a
+// range the search has to walk through.  One CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) uniq_kernel(const uint64_t* __restrict__ spl, LearnMeta* meta,
+                                                    uint64_t* __restrict__ uniq, uint16_t* __restrict__ cum)
+{
+    constexpr int PER = (NSPLIT + 1) / 1024;
+    __shared__ uint32_t wsum[32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    bool f[PER];
+    uint32_t c = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int j = t * PER + q;
+        f[q] = j < NSPLIT && (j == 0 || spl[j] != spl[j - 1]);
+        c += f[q];
+    }
+    uint32_t x = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = wsum[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, w, d);
+            if (lane >= d) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    uint32_t pos = x - c + (wid > 0 ? wsum[wid - 1] : 0u);
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int j = t * PER + q;
+        if (f[q]) {
+            uniq[pos] = spl[j];
+            cum[pos] = (uint16_t)j;
+            ++pos;
+        }
+    }
+    if (t == 1023) {
+        cum[pos] = (uint16_t)NSPLIT;
+        meta->nuniq = (int)pos;
+    }
+}
+
+// T[b] = number of distinct splitter values whose fine bin is below b, for
+// b = 0 .. nfine.  Since the fine bin never decreases with the prefix, a key
+// in fine bin b has at least T[b] and at most T[b+1] distinct values at or
+// below it, so its bucket is found by a search among those few (this holds
+// for any array of splitters: the outcome of a binary search never decreases
+// with the key).  The table is read through L2 by every key.
+__global__ void __launch_bounds__(256) table_kernel(const uint64_t* __restrict__ uniq,
+                                                    const uint32_t* __restrict__ coarse,
+                                                    const LearnMeta* __restrict__ meta, uint16_t* __restrict__ table)
+{
+    __shared__ int32_t s_beta[NSPLIT];
+    __shared__ uint32_t s_coarse[NCOARSE];
+    for (int i = threadIdx.x; i < NCOARSE; i += blockDim.x) s_coarse[i] = coarse[i];
     __syncthreads();
     const uint64_t lo53 = meta->lo53, range = meta->range;
-    const int sh = meta->sh;
-    const int64_t nb = (1ll << TABLE_BITS) + 1;
-    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t d = (uint64_t)b << sh;
-        table[b] = (uint16_t)(d > range ? NSPLIT : count_le(s_spl, lo53 + d));
+    const int sh = meta->sh, m = meta->nuniq, nfine = meta->nfine;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        const uint64_t u = uniq[k];
+        // splitters lie in [lo53, lo53 + range + 1]; one above the range counts above every bin
+        s_beta[k] = u < lo53 ? -1 : (u - lo53 > range ? nfine : (int32_t)fine_bin(s_coarse, u - lo53, sh));
+    }
+    __syncthreads();
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= nfine; b += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = m;                               // number of k with s_beta[k] < b
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_beta[mid] < b) lo = mid + 1;
+            else hi = mid;
+        }
+        table[b] = (uint16_t)lo;
     }
 }
 
 // ---------------------------------------------------------------- partition
-// The bucket of a key: number of splitters at or below its 53-bit prefix, from
-// the table and a short search among the splitters of its bin (shared memory).
-__device__ __forceinline__ int bucket_of(const uint64_t* s_spl, const uint16_t* __restrict__ table, uint64_t raw,
-                                         int mode, uint64_t lo53, uint64_t range, int sh)
-{
-    const uint64_t e53 = encode_key(raw, mode) >> 11;
-    if (e53 < lo53) return 0;
-    const uint64_t d = e53 - lo53;
-    if (d > range) return NSPLIT;                     // above every splitter
-    const int64_t b = (int64_t)(d >> sh);
-    int lo = __ldg(&table[b]), hi = __ldg(&table[b + 1]);
-    while (lo < hi) {                                 // largest c in [lo, hi] with spl[c-1] <= e53
-        int mid = (lo + hi + 1) >> 1;
-        if (s_spl[mid - 1] <= e53) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-// Pass-A histogram.  Every key's bucket is evaluated here, once, and written
-// to bid[i]; per tile the counts of its low 6 bits go to
+// Pass-A histogram.  Every key's bucket -- the number of splitters at or below
+// its 53-bit prefix: from the key's fine bin, the table's range of distinct
+// splitter values, a short search among them and their splitter counts (all
+// but the table in shared memory) -- is evaluated here, once, and written to
+// bid[i]; per tile the counts of its low 6 bits go to
 // counts[digit * ntiles + tile] (per-warp shared sub-histograms), and every
 // bucket's total is accumulated (per-CTA shared histogram, one global atomic
 // per touched bucket at the end).
 constexpr int HIST_THREADS = 256;
 
-__global__ void __launch_bounds__(HIST_THREADS)
+__global__ void __launch_bounds__(HIST_THREADS, 3)   // three CTAs per SM
     part_hist_a_kernel(const uint64_t* __restrict__ keys, int64_t n, int mode, const uint16_t* __restrict__ table,
-                       const uint64_t* __restrict__ spl, const LearnMeta* __restrict__ meta,
+                       const uint32_t* __restrict__ coarse, const uint64_t* __restrict__ uniq,
+                       const uint16_t* __restrict__ cum, const LearnMeta* __restrict__ meta,
                        uint16_t* __restrict__ bid, uint32_t* __restrict__ counts, int64_t ntiles,
                        unsigned long long* btot, int bucket_xor)
 {
-    __shared__ uint64_t s_spl[NSPLIT];
+    constexpr int R = PART_TILE / HIST_THREADS;
+    __shared__ uint64_t s_uniq[NSPLIT];
+    __shared__ uint16_t s_cum[NSPLIT + 1];
+    __shared__ uint32_t s_coarse[NCOARSE];
     __shared__ uint32_t bcnt[NBUCKETS];
     __shared__ uint32_t wcnt[HIST_THREADS / 32][64];
     const int w = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < NSPLIT; i += blockDim.x) s_spl[i] = spl[i];
+    const int m = meta->nuniq;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s_uniq[i] = uniq[i];
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) s_cum[i] = cum[i];
+    for (int i = threadIdx.x; i < NCOARSE; i += blockDim.x) s_coarse[i] = coarse[i];
     for (int i = threadIdx.x; i < NBUCKETS; i += blockDim.x) bcnt[i] = 0;
     for (int i = threadIdx.x; i < (HIST_THREADS / 32) * 64; i += blockDim.x) (&wcnt[0][0])[i] = 0;
     const uint64_t lo53 = meta->lo53, range = meta->range;
     const int sh = meta->sh;
     __syncthreads();
+    // The keys of the next tile are loaded while this tile's buckets are
+    // resolved, and every table lookup of a tile is issued before the first is
+    // used: one HBM and one L2 round trip per tile instead of one per key.
+    uint64_t raw[R];
+    auto load_tile = [&](int64_t tile, uint64_t (&dst)[R]) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int64_t i = tile * PART_TILE + threadIdx.x + r * HIST_THREADS;
+            dst[r] = (tile < ntiles && i < n) ? keys[i] : 0ull;
+        }
+    };
+    load_tile(blockIdx.x, raw);
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t base = tile * PART_TILE;
-        uint64_t raw[PART_TILE / HIST_THREADS];
+        uint64_t e53[R];
+        int lo[R], hi[R];
 #pragma unroll
-        for (int r = 0; r < PART_TILE / HIST_THREADS; ++r) {
-            const int64_t i = base + threadIdx.x + r * HIST_THREADS;
-            raw[r] = i < n ? keys[i] : 0ull;
+        for (int r = 0; r < R; ++r) {
+            // the number of distinct splitter values at or below the key lies
+            // in [lo, hi]: none below the sample range, all above it, else
+            // the table's range for the key's fine bin
+            e53[r] = encode_key(raw[r], mode) >> 11;
+            const bool below = e53[r] < lo53;
+            const uint64_t d = below ? 0 : e53[r] - lo53;
+            if (below) {
+                lo[r] = hi[r] = 0;
+            } else if (d > range) {
+                lo[r] = hi[r] = m;
+            } else {
+                const int64_t fb = fine_bin(s_coarse, d, sh);
+                lo[r] = __ldg(&table[fb]);
+                hi[r] = __ldg(&table[fb + 1]);
+            }
         }
+        uint64_t nraw[R];
+        load_tile(tile + gridDim.x, nraw);
 #pragma unroll
-        for (int r = 0; r < PART_TILE / HIST_THREADS; ++r) {
+        for (int r = 0; r < R; ++r) {
             const int64_t i = base + threadIdx.x + r * HIST_THREADS;
             if (i < n) {
+                int l = lo[r], h = hi[r];
+                while (l < h) {                           // largest c in [l, h] with uniq[c-1] <= e53
+                    const int mid = (l + h + 1) >> 1;
+                    if (s_uniq[mid - 1] <= e53[r]) l = mid;
+                    else h = mid - 1;
+                }
                 // bucket_xor is 0 except under the test hook that swaps bucket pairs
-                const int bk = bucket_of(s_spl, table, raw[r], mode, lo53, range, sh) ^ bucket_xor;
+                const int bk = (int)s_cum[l] ^ bucket_xor;
                 bid[i] = (uint16_t)bk;
                 atomicAdd(&wcnt[w][bk & 63], 1u);
                 atomicAdd(&bcnt[bk], 1u);
@@ -542,6 +691,8 @@ __global__ void __launch_bounds__(HIST_THREADS)
             counts[(int64_t)threadIdx.x * ntiles + tile] = c;
         }
         __syncthreads();
+#pragma unroll
+        for (int r = 0; r < R; ++r) raw[r] = nraw[r];
     }
     for (int i = threadIdx.x; i < NBUCKETS; i += blockDim.x)
         if (bcnt[i]) atomicAdd(&btot[i], (unsigned long long)bcnt[i]);
@@ -627,13 +778,40 @@ struct ScatterSmem {
     int64_t dbase[64];
 };
 
+// One tile's inputs for part_scatter_kernel: this warp's 256 keys, in input
+// order (element tile * PART_TILE + 256 w + 32 r + lane), with payload, bucket
+// id and digit (64 past the end: not placed), and the tile's offset within
+// digit t.  A tile past the last gets only end markers.
+__device__ __forceinline__ void scatter_load_tile(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sv,
+                                                  const uint16_t* __restrict__ sbid,
+                                                  const uint32_t* __restrict__ counts, int64_t n, int64_t ntiles,
+                                                  int shift, int64_t tile, int t, int w, int lane,
+                                                  uint64_t (&kk)[PART_ITEMS], uint32_t (&vv)[PART_ITEMS],
+                                                  int (&bb)[PART_ITEMS], int (&dd)[PART_ITEMS], uint32_t& my_cnt)
+{
+    my_cnt = (t < 64 && tile < ntiles) ? counts[(int64_t)t * ntiles + tile] : 0u;
+#pragma unroll
+    for (int r = 0; r < PART_ITEMS; ++r) {
+        const int64_t i = tile * PART_TILE + w * 256 + r * 32 + lane;
+        if (tile < ntiles && i < n) {
+            kk[r] = sk[i];
+            vv[r] = sv ? sv[i] : 0u;
+            bb[r] = sbid[i];
+            dd[r] = (bb[r] >> shift) & 63;
+        } else {
+            bb[r] = 0;
+            dd[r] = 64;
+        }
+    }
+}
+
 // Stable 64-way scatter of one pass, digit = (bucket id >> shift) & 63: within a
 // tile every warp ranks its 256 consecutive keys in input order (match_any
 // groups, per-warp counters), the tile is laid out by digit in shared memory,
 // and every digit's run is written contiguously to its place: digit base +
 // this tile's offset in the digit.  The bucket ids travel with the keys when
 // db is given.
-__global__ void __launch_bounds__(PART_THREADS)
+__global__ void __launch_bounds__(PART_THREADS, 3)   // three CTAs per SM (the launch keeps all resident)
     part_scatter_kernel(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sv,
                         const uint16_t* __restrict__ sbid, uint64_t* __restrict__ dk, uint32_t* __restrict__ dv,
                         uint16_t* __restrict__ dbid, int64_t n, int shift, const uint32_t* __restrict__ counts,
@@ -651,27 +829,15 @@ __global__ void __launch_bounds__(PART_THREADS)
     for (int i = t; i < (PART_THREADS / 32) * 64; i += PART_THREADS) (&S.wcnt[0][0])[i] = 0;
     const unsigned lt_mask = (1u << lane) - 1u;
     __syncthreads();
+    uint64_t kk[PART_ITEMS];
+    uint32_t vv[PART_ITEMS];
+    int bb[PART_ITEMS], dd[PART_ITEMS], rr[PART_ITEMS];
+    uint32_t my_cnt = 0;
+    // the loads of the next tile are issued before this tile's write-out, so
+    // that they overlap it
+    scatter_load_tile(sk, sv, sbid, counts, n, ntiles, shift, blockIdx.x, t, w, lane, kk, vv, bb, dd, my_cnt);
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t base = tile * PART_TILE;
-        // this tile's offset within digit t, loaded with the data (not after the barriers below)
-        const uint32_t my_cnt = t < 64 ? counts[(int64_t)t * ntiles + tile] : 0u;
-        uint64_t kk[PART_ITEMS];
-        uint32_t vv[PART_ITEMS];
-        int bb[PART_ITEMS], dd[PART_ITEMS], rr[PART_ITEMS];
-        // this warp's 256 keys, in input order: element base + 256 w + 32 r + lane
-#pragma unroll
-        for (int r = 0; r < PART_ITEMS; ++r) {
-            const int64_t i = base + w * 256 + r * 32 + lane;
-            if (i < n) {
-                kk[r] = sk[i];
-                vv[r] = sv ? sv[i] : 0u;
-                bb[r] = sbid[i];
-                dd[r] = (bb[r] >> shift) & 63;
-            } else {
-                bb[r] = 0;
-                dd[r] = 64;                               // past the end: not placed
-            }
-        }
 #pragma unroll
         for (int r = 0; r < PART_ITEMS; ++r) {
             // lanes with the same digit, from one ballot per digit bit (digit 64
@@ -726,6 +892,7 @@ __global__ void __launch_bounds__(PART_THREADS)
             }
         }
         __syncthreads();
+        scatter_load_tile(sk, sv, sbid, counts, n, ntiles, shift, tile + gridDim.x, t, w, lane, kk, vv, bb, dd, my_cnt);
         const int cnt = (int)imin64(PART_TILE, n - base);
         for (int i = t; i < cnt; i += PART_THREADS) {
             const int64_t g = S.gbase[S.sd[i]] + i;
@@ -945,7 +1112,8 @@ void init_params_host(float* p)
 // rest until the end of the call.
 struct LearnLayout {
     size_t bufk, bufv, bidA, bidB, counts, big;
-    size_t sample, x, t, params, F, spl, spl_raw, table, meta, rowtot, btot, diff, tied, off, loss, ctl, total;
+    size_t sample, x, t, params, F, spl, spl_raw, table, coarse, uniq, cum, meta, rowtot, btot, diff, tied, off, loss, ctl,
+        total;
     int64_t ntiles;
 };
 
@@ -967,7 +1135,10 @@ LearnLayout learn_layout(int64_t n, bool with_vals)
     o.params = off; off += align256((size_t)2 * NP * 4);
     o.F = off; off += align256((size_t)GRID_G * 4);
     o.spl = off; off += align256((size_t)(NSPLIT + 1) * 8);
-    o.table = off; off += align256(((size_t)(1 << TABLE_BITS) + 1) * 2);
+    o.table = off; off += align256(((size_t)TABLE_MAX + 1) * 2);
+    o.coarse = off; off += align256((size_t)NCOARSE * 4);
+    o.uniq = off; off += align256((size_t)NSPLIT * 8);
+    o.cum = off; off += align256((size_t)(NSPLIT + 1) * 2);
     o.spl_raw = off; off += align256((size_t)(NSPLIT + 1) * 8);
     o.meta = off; off += align256(sizeof(LearnMeta));
     o.rowtot = off; off += align256(64 * 8);
@@ -1051,8 +1222,14 @@ int learn_fit_phase(const uint64_t* keys, int64_t n, int mode, const gns_learned
     if (fault == GNS_FAULT_SPLITTERS_REVERSED) {
         FTRY(launch(K_LEARN_SPLIT, fault_reverse_splitters_kernel, dim3(cdiv(NSPLIT, 256)), dim3(256), 0, s, spl));
     }
-    FTRY(launch(K_LEARN_SPLIT, table_kernel, dim3((unsigned)(sms * 4)), dim3(256), 0, s, (const uint64_t*)spl,
-                (const LearnMeta*)meta, table));
+    uint32_t* coarse = (uint32_t*)(ws + lay.coarse);
+    uint64_t* uniq = (uint64_t*)(ws + lay.uniq);
+    uint16_t* cum = (uint16_t*)(ws + lay.cum);
+    FTRY(launch(K_LEARN_SPLIT, coarse_kernel, dim3(1), dim3(NCOARSE), 0, s, (const uint64_t*)sample, mode, meta,
+                coarse));
+    FTRY(launch(K_LEARN_SPLIT, uniq_kernel, dim3(1), dim3(1024), 0, s, (const uint64_t*)spl, meta, uniq, cum));
+    FTRY(launch(K_LEARN_SPLIT, table_kernel, dim3((unsigned)(sms * 4)), dim3(256), 0, s, (const uint64_t*)uniq,
+                (const uint32_t*)coarse, (const LearnMeta*)meta, table));
 #undef FTRY
     return GNS_OK;
 }
@@ -1085,6 +1262,9 @@ int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, con
     uint32_t* counts = xs ? xs->counts : (uint32_t*)(big + lay.counts);
     uint64_t* spl = (uint64_t*)(ws + lay.spl);
     uint16_t* table = (uint16_t*)(ws + lay.table);
+    uint32_t* coarse = (uint32_t*)(ws + lay.coarse);
+    uint64_t* uniq = (uint64_t*)(ws + lay.uniq);
+    uint16_t* cum = (uint16_t*)(ws + lay.cum);
     LearnMeta* meta = (LearnMeta*)(ws + lay.meta);
     unsigned long long* rowtot = (unsigned long long*)(ws + lay.rowtot);
     unsigned long long* btot = (unsigned long long*)(ws + lay.btot);
@@ -1111,6 +1291,9 @@ int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, con
         // the fit of an earlier call: its splitters and table, a copy of its meta
         spl = (uint64_t*)(fitted + lay.spl);
         table = (uint16_t*)(fitted + lay.table);
+        coarse = (uint32_t*)(fitted + lay.coarse);
+        uniq = (uint64_t*)(fitted + lay.uniq);
+        cum = (uint16_t*)(fitted + lay.cum);
         LTRY(cudaMemcpyAsync(meta, fitted + lay.meta, sizeof(LearnMeta), cudaMemcpyDeviceToDevice, s));
         LTRY(cudaMemcpyAsync(loss, fitted + lay.loss, sizeof(float), cudaMemcpyDeviceToDevice, s));
     } else {
@@ -1122,10 +1305,10 @@ int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, con
 
     {
         // pass A: buckets evaluated once (-> bidA), stable scatter by the low 6 bits
-        const int64_t hgrid = imin_h(ntiles, (int64_t)sms * 4);
+        const int64_t hgrid = imin_h(ntiles, (int64_t)sms * 3);
         LTRY(launch(K_LEARN_HIST, part_hist_a_kernel, dim3((unsigned)hgrid), dim3(HIST_THREADS), 0, s,
-                    (const uint64_t*)keys, n, mode, (const uint16_t*)table, (const uint64_t*)spl,
-                    (const LearnMeta*)meta, bidA, counts, ntiles, btot,
+                    (const uint64_t*)keys, n, mode, (const uint16_t*)table, (const uint32_t*)coarse,
+                    (const uint64_t*)uniq, (const uint16_t*)cum, (const LearnMeta*)meta, bidA, counts, ntiles, btot,
                     fault == GNS_FAULT_BUCKETS_SWAPPED ? 1 : 0));
         LTRY(launch(K_LEARN_SCAN, row_scan_kernel, dim3(64), dim3(1024), 0, s, counts, ntiles, rowtot));
         const int64_t sgrid = imin_h(ntiles, (int64_t)sms * 3);   // all CTAs resident
