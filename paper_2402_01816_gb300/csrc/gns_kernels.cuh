@@ -81,7 +81,9 @@ __device__ __forceinline__ int64_t merge_path(int64_t diag, int64_t na, int64_t 
 // them.  The decision "take A" tests both bounds itself, so a run's head is
 // reloaded without a bounds test: past the end of run A it reads run B's
 // first element, past the end of run B at most one slot past the tile (the
-// spare slot of SmemKV), and the value is never used.
+// spare slot of SmemKV), and the value is never used.  The reload is one load
+// from the taken element's successor, whichever run it is in (one load
+// instruction per output instead of one per run).
 template <int N, int ITEMS>
 __device__ __forceinline__ void serial_merge(const SmemKV<N>& sm, int i, int ie, int j, int je,
                                              uint64_t (&k)[ITEMS], uint32_t (&v)[ITEMS])
@@ -94,12 +96,13 @@ __device__ __forceinline__ void serial_merge(const SmemKV<N>& sm, int i, int ie,
         const int src = takeA ? i : j;
         k[x] = takeA ? ka : kb;
         v[x] = sm.v[pidx(src)];
+        const uint64_t next = sm.k[pidx(src + 1)];
         if (takeA) {
             ++i;
-            ka = sm.k[pidx(i)];
+            ka = next;
         } else {
             ++j;
-            kb = sm.k[pidx(j)];
+            kb = next;
         }
     }
 }
