@@ -255,7 +255,9 @@ def learned_vs_plain(dev, n=1 << 28):
     peak, peak_kind = load_peaks()
     part_b = 66 * n                                   # histogram 10, scatter A 28, scan 2, scatter B 26 per key
     mean_bucket = n / 4096.0
-    bucket_passes = 1 + max(0, math.ceil(math.log2(max(1.0, mean_bucket / 4096))))
+    # buckets sorted at global 8192-key tiles: a bucket of L keys touches about
+    # L / 8192 + 1 tiles and takes ceil(log2(tiles)) merge levels
+    bucket_passes = 1 + max(0, math.ceil(math.log2(mean_bucket / 8192 + 1)))
     bs_b = 24 * n * bucket_passes
     roof = {"bound": "hbm", "peak": peak, "unit": "GB/s", "peak_kind": peak_kind,
             "partition": {"algorithmic_bytes": part_b, "achieved": part_b / (rep["partition_ms"] / 1e3) / 1e9,
@@ -265,7 +267,7 @@ def learned_vs_plain(dev, n=1 << 28):
                             "achieved": bs_b / (rep["bucket_sort_ms"] / 1e3) / 1e9,
                             "frac": bs_b / (rep["bucket_sort_ms"] / 1e3) / 1e9 / peak,
                             "bytes_model": f"24 B per key per pass, {bucket_passes} passes of a mean-sized bucket "
-                                           "(1 tile pass + ceil(log2(L/4096)) levels)"}}
+                                           "(1 tile pass + ceil(log2(L/8192 + 1)) levels)"}}
     return {"workload": "learned-splitter sort: 2^28 float64 keys (40% log-normal sigma 2, 30% Zipf s=1.2 "
                         "over 2^16 integers, 30% mix of 8 Gaussians) + uint32 index payload, 4096 buckets",
             "roofline": roof,

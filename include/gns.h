@@ -260,13 +260,15 @@ void gns_segmented_release(gns_stream_t stream);
  *      stable sort, however good or bad the network is.  The 4096-way stable
  *      partition is two 64-way stable scatter passes (low, then high 6 bits of
  *      the bucket).
- *   3. bucket sort: every bucket is a segment for the segmented sort, except
- *      buckets whose keys are all bit-identical, which a stable partition has
- *      already left in their final order (the DIET idea of the paper's
- *      "DIET-method" section: an all-tied part needs no sorting); a bucket
- *      that came out larger than `overfull_factor` times the mean is simply
- *      sorted by more merge levels of the same merge path (the plain merge
- *      path is the fallback for it).
+ *   3. bucket sort: the buckets are ordered, so the array is tile-sorted at
+ *      its global 8192-key tiles (a tile may hold the ends of several
+ *      buckets) and every bucket that spans tiles is finished by merge levels
+ *      over its own runs; buckets whose keys are all bit-identical, which a
+ *      stable partition has already left in their final order, are skipped
+ *      (the DIET idea of the paper's "DIET-method" section: an all-tied part
+ *      needs no sorting); a bucket that came out larger than
+ *      `overfull_factor` times the mean is simply sorted by more merge levels
+ *      of the same merge path (the plain merge path is the fallback for it).
  *   4. check and fallback: after the bucket sort every bucket is sorted, so its
  *      first and last keys are its minimum and maximum; the check requires the
  *      bucket offsets to partition [0, n) and, at every bucket boundary, the

@@ -5,7 +5,7 @@
 // monotone function of its order-mapped 53-bit prefix (the number of splitters
 // at or below it), so equal keys share a bucket and stably sorting every bucket
 // after a stable partition gives exactly the stable sort.  The network only
-// decides where the 4095 splitters go.
+// decides where the NSPLIT = 4095 splitters go.
 #include <cooperative_groups.h>
 #include <math.h>
 #include <stdlib.h>
@@ -36,7 +36,14 @@ constexpr unsigned FULL = 0xffffffffu;
 
 constexpr int SAMPLE_M = 1 << 16;     // sample size (power of two)
 constexpr int GRID_G = 1 << 16;       // grid for inverting the fitted CDF
-constexpr int NBUCKETS = 4096;
+// Bucket ids: two stable LSD scatter passes of DIGIT_BITS bits.  Measured with
+// 7 (16384 buckets) at 2^28 keys of the mixture: the bucket merges shorter
+// (4.8 -> 3.3 ms) but the 128-way scatters slower (4.6 -> 5.4 ms), the
+// half-buffer form slower, and on log-normal keys the trained network made
+// the largest bucket larger than the first stage's.
+constexpr int DIGIT_BITS = 6;
+constexpr int RADIX = 1 << DIGIT_BITS;
+constexpr int NBUCKETS = RADIX * RADIX;   // 4096
 constexpr int NSPLIT = NBUCKETS - 1;
 constexpr int TABLE_BITS = 22;        // about 2^22 fine bins of the key -> bucket-range table (global, L2-resident)
 constexpr int COARSE_BITS = 10;       // coarse bins, uniform in the prefix space, that share the fine bins out
@@ -414,8 +421,8 @@ __global__ void __launch_bounds__(1024) running_max_kernel(float* F)
     }
 }
 
-// Splitter j (1..4095): the prefix of the first grid point where the monotone
-// CDF reaches j / 4096.
+// Splitter j (1..NSPLIT): the prefix of the first grid point where the
+// monotone CDF reaches j / NBUCKETS.
 __global__ void splitter_kernel(const float* __restrict__ F, LearnMeta* meta, uint64_t* __restrict__ spl)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x + 1;
@@ -597,34 +604,28 @@ __global__ void __launch_bounds__(256) table_kernel(const uint64_t* __restrict__
 // ---------------------------------------------------------------- partition
 // Pass-A histogram.  Every key's bucket -- the number of splitters at or below
 // its 53-bit prefix: from the key's fine bin, the table's range of distinct
-// splitter values, a short search among them and their splitter counts (all
-// but the table in shared memory) -- is evaluated here, once, and written to
-// bid[i]; per tile the counts of its low 6 bits go to
-// counts[digit * ntiles + tile] (per-warp shared sub-histograms), and every
-// bucket's total is accumulated (per-CTA shared histogram, one global atomic
-// per touched bucket at the end).
+// splitter values, a short search among them (rarely more than one step) and
+// their splitter counts -- is evaluated here, once, and written to bid[i]; per
+// tile the counts of its low DIGIT_BITS bits go to counts[digit * ntiles +
+// tile] (per-warp shared sub-histograms).  The buckets' totals are read off
+// the partitioned bucket ids afterwards (bucket_bounds_kernel).
 constexpr int HIST_THREADS = 256;
 
-__global__ void __launch_bounds__(HIST_THREADS, 3)   // three CTAs per SM
+__global__ void __launch_bounds__(HIST_THREADS, 4)   // four CTAs per SM
     part_hist_a_kernel(const uint64_t* __restrict__ keys, int64_t n, int mode, const uint16_t* __restrict__ table,
                        const uint32_t* __restrict__ coarse, const uint64_t* __restrict__ uniq,
                        const uint16_t* __restrict__ cum, const LearnMeta* __restrict__ meta,
-                       uint16_t* __restrict__ bid, uint32_t* __restrict__ counts, int64_t ntiles,
-                       unsigned long long* btot, int bucket_xor)
+                       uint16_t* __restrict__ bid, uint32_t* __restrict__ counts, int64_t ntiles, int bucket_xor)
 {
     constexpr int R = PART_TILE / HIST_THREADS;
-    __shared__ uint64_t s_uniq[NSPLIT];
     __shared__ uint16_t s_cum[NSPLIT + 1];
     __shared__ uint32_t s_coarse[NCOARSE];
-    __shared__ uint32_t bcnt[NBUCKETS];
-    __shared__ uint32_t wcnt[HIST_THREADS / 32][64];
+    __shared__ uint32_t wcnt[HIST_THREADS / 32][RADIX];
     const int w = threadIdx.x >> 5;
     const int m = meta->nuniq;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) s_uniq[i] = uniq[i];
     for (int i = threadIdx.x; i <= m; i += blockDim.x) s_cum[i] = cum[i];
     for (int i = threadIdx.x; i < NCOARSE; i += blockDim.x) s_coarse[i] = coarse[i];
-    for (int i = threadIdx.x; i < NBUCKETS; i += blockDim.x) bcnt[i] = 0;
-    for (int i = threadIdx.x; i < (HIST_THREADS / 32) * 64; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < (HIST_THREADS / 32) * RADIX; i += blockDim.x) (&wcnt[0][0])[i] = 0;
     const uint64_t lo53 = meta->lo53, range = meta->range;
     const int sh = meta->sh;
     __syncthreads();
@@ -669,20 +670,19 @@ __global__ void __launch_bounds__(HIST_THREADS, 3)   // three CTAs per SM
             const int64_t i = base + threadIdx.x + r * HIST_THREADS;
             if (i < n) {
                 int l = lo[r], h = hi[r];
-                while (l < h) {                           // largest c in [l, h] with uniq[c-1] <= e53
+                while (l < h) {                           // largest c in [l, h] with uniq[c-1] <= e53 (rare)
                     const int mid = (l + h + 1) >> 1;
-                    if (s_uniq[mid - 1] <= e53[r]) l = mid;
+                    if (__ldg(&uniq[mid - 1]) <= e53[r]) l = mid;
                     else h = mid - 1;
                 }
                 // bucket_xor is 0 except under the test hook that swaps bucket pairs
                 const int bk = (int)s_cum[l] ^ bucket_xor;
                 bid[i] = (uint16_t)bk;
-                atomicAdd(&wcnt[w][bk & 63], 1u);
-                atomicAdd(&bcnt[bk], 1u);
+                atomicAdd(&wcnt[w][bk & (RADIX - 1)], 1u);
             }
         }
         __syncthreads();
-        if (threadIdx.x < 64) {
+        if (threadIdx.x < RADIX) {
             uint32_t c = 0;
             for (int q = 0; q < HIST_THREADS / 32; ++q) {
                 c += wcnt[q][threadIdx.x];
@@ -694,27 +694,26 @@ __global__ void __launch_bounds__(HIST_THREADS, 3)   // three CTAs per SM
 #pragma unroll
         for (int r = 0; r < R; ++r) raw[r] = nraw[r];
     }
-    for (int i = threadIdx.x; i < NBUCKETS; i += blockDim.x)
-        if (bcnt[i]) atomicAdd(&btot[i], (unsigned long long)bcnt[i]);
 }
 
-// Pass-B histogram: per tile, counts of the high 6 bits of the stored bucket ids.
+// Pass-B histogram: per tile, counts of the high DIGIT_BITS bits of the stored
+// bucket ids.
 __global__ void __launch_bounds__(256) part_hist_b_kernel(const uint16_t* __restrict__ bid, int64_t n,
                                                           uint32_t* __restrict__ counts, int64_t ntiles)
 {
-    __shared__ uint32_t wcnt[8][64];
+    __shared__ uint32_t wcnt[8][RADIX];
     const int w = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < 8 * 64; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < 8 * RADIX; i += blockDim.x) (&wcnt[0][0])[i] = 0;
     __syncthreads();
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t base = tile * PART_TILE;
 #pragma unroll
         for (int r = 0; r < PART_TILE / 256; ++r) {
             const int64_t i = base + threadIdx.x + r * 256;
-            if (i < n) atomicAdd(&wcnt[w][bid[i] >> 6], 1u);
+            if (i < n) atomicAdd(&wcnt[w][bid[i] >> DIGIT_BITS], 1u);
         }
         __syncthreads();
-        if (threadIdx.x < 64) {
+        if (threadIdx.x < RADIX) {
             uint32_t c = 0;
             for (int q = 0; q < 8; ++q) {
                 c += wcnt[q][threadIdx.x];
@@ -772,15 +771,15 @@ struct ScatterSmem {
     uint32_t sv[PART_TILE];
     uint16_t sb[PART_TILE];
     uint8_t sd[PART_TILE];
-    uint32_t wcnt[PART_THREADS / 32][64];
-    uint32_t dstart[64];
-    int64_t gbase[64];
-    int64_t dbase[64];
+    uint32_t wcnt[PART_THREADS / 32][RADIX];
+    uint32_t dstart[RADIX];
+    int64_t gbase[RADIX];
+    int64_t dbase[RADIX];
 };
 
 // One tile's inputs for part_scatter_kernel: this warp's 256 keys, in input
 // order (element tile * PART_TILE + 256 w + 32 r + lane), with payload, bucket
-// id and digit (64 past the end: not placed), and the tile's offset within
+// id and digit (RADIX past the end: not placed), and the tile's offset within
 // digit t.  A tile past the last gets only end markers.
 __device__ __forceinline__ void scatter_load_tile(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sv,
                                                   const uint16_t* __restrict__ sbid,
@@ -789,7 +788,7 @@ __device__ __forceinline__ void scatter_load_tile(const uint64_t* __restrict__ s
                                                   uint64_t (&kk)[PART_ITEMS], uint32_t (&vv)[PART_ITEMS],
                                                   int (&bb)[PART_ITEMS], int (&dd)[PART_ITEMS], uint32_t& my_cnt)
 {
-    my_cnt = (t < 64 && tile < ntiles) ? counts[(int64_t)t * ntiles + tile] : 0u;
+    my_cnt = (t < RADIX && tile < ntiles) ? counts[(int64_t)t * ntiles + tile] : 0u;
 #pragma unroll
     for (int r = 0; r < PART_ITEMS; ++r) {
         const int64_t i = tile * PART_TILE + w * 256 + r * 32 + lane;
@@ -797,15 +796,15 @@ __device__ __forceinline__ void scatter_load_tile(const uint64_t* __restrict__ s
             kk[r] = sk[i];
             vv[r] = sv ? sv[i] : 0u;
             bb[r] = sbid[i];
-            dd[r] = (bb[r] >> shift) & 63;
+            dd[r] = (bb[r] >> shift) & (RADIX - 1);
         } else {
             bb[r] = 0;
-            dd[r] = 64;
+            dd[r] = RADIX;
         }
     }
 }
 
-// Stable 64-way scatter of one pass, digit = (bucket id >> shift) & 63: within a
+// Stable RADIX-way scatter of one pass, digit = (bucket id >> shift) mod RADIX: within a
 // tile every warp ranks its 256 consecutive keys in input order (match_any
 // groups, per-warp counters), the tile is laid out by digit in shared memory,
 // and every digit's run is written contiguously to its place: digit base +
@@ -821,12 +820,12 @@ __global__ void __launch_bounds__(PART_THREADS, 3)   // three CTAs per SM (the l
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     if (t == 0) {
         int64_t run = 0;
-        for (int d = 0; d < 64; ++d) {
+        for (int d = 0; d < RADIX; ++d) {
             S.dbase[d] = run;
             run += (int64_t)rowtot[d];
         }
     }
-    for (int i = t; i < (PART_THREADS / 32) * 64; i += PART_THREADS) (&S.wcnt[0][0])[i] = 0;
+    for (int i = t; i < (PART_THREADS / 32) * RADIX; i += PART_THREADS) (&S.wcnt[0][0])[i] = 0;
     const unsigned lt_mask = (1u << lane) - 1u;
     __syncthreads();
     uint64_t kk[PART_ITEMS];
@@ -840,24 +839,24 @@ __global__ void __launch_bounds__(PART_THREADS, 3)   // three CTAs per SM (the l
         const int64_t base = tile * PART_TILE;
 #pragma unroll
         for (int r = 0; r < PART_ITEMS; ++r) {
-            // lanes with the same digit, from one ballot per digit bit (digit 64
-            // marks a lane past the end: bit 6)
+            // lanes with the same digit, from one ballot per digit bit (digit
+            // RADIX marks a lane past the end: bit DIGIT_BITS)
             unsigned grp = FULL;
 #pragma unroll
-            for (int bit = 0; bit < 7; ++bit) {
+            for (int bit = 0; bit <= DIGIT_BITS; ++bit) {
                 const unsigned bl = __ballot_sync(FULL, (dd[r] >> bit) & 1);
                 grp &= ((dd[r] >> bit) & 1) ? bl : ~bl;
             }
             const int leader = __ffs(grp) - 1;
             uint32_t pre = 0;
-            if (dd[r] < 64) pre = S.wcnt[w][dd[r]];
+            if (dd[r] < RADIX) pre = S.wcnt[w][dd[r]];
             __syncwarp();
-            if (dd[r] < 64 && lane == leader) S.wcnt[w][dd[r]] = pre + (uint32_t)__popc(grp);
+            if (dd[r] < RADIX && lane == leader) S.wcnt[w][dd[r]] = pre + (uint32_t)__popc(grp);
             __syncwarp();
             rr[r] = (int)(pre + (uint32_t)__popc(grp & lt_mask));
         }
         __syncthreads();
-        if (t < 64) {                                     // each digit: warp-major prefix
+        if (t < RADIX) {                                  // each digit: warp-major prefix
             uint32_t tot = 0;
             for (int q = 0; q < PART_THREADS / 32; ++q) {
                 const uint32_t c = S.wcnt[q][t];
@@ -867,23 +866,32 @@ __global__ void __launch_bounds__(PART_THREADS, 3)   // three CTAs per SM (the l
             S.dstart[t] = tot;                            // total for now
         }
         __syncthreads();
-        if (t < 32) {                                     // exclusive scan of the 64 totals (one warp)
-            const uint32_t a = S.dstart[2 * t], b = S.dstart[2 * t + 1];
-            uint32_t x = a + b;
+        if (t < 32) {                                     // exclusive scan of the RADIX totals (one warp)
+            constexpr int PL = RADIX / 32;                // digits per lane
+            uint32_t c[PL], x = 0;
+#pragma unroll
+            for (int q = 0; q < PL; ++q) {
+                c[q] = S.dstart[PL * t + q];
+                x += c[q];
+            }
+            const uint32_t own = x;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
                 const uint32_t y = __shfl_up_sync(FULL, x, d);
                 if (t >= d) x += y;
             }
-            const uint32_t excl = x - (a + b);
-            S.dstart[2 * t] = excl;
-            S.dstart[2 * t + 1] = excl + a;
+            uint32_t run = x - own;
+#pragma unroll
+            for (int q = 0; q < PL; ++q) {
+                S.dstart[PL * t + q] = run;
+                run += c[q];
+            }
         }
         __syncthreads();
-        if (t < 64) S.gbase[t] = S.dbase[t] + (int64_t)my_cnt - (int64_t)S.dstart[t];
+        if (t < RADIX) S.gbase[t] = S.dbase[t] + (int64_t)my_cnt - (int64_t)S.dstart[t];
 #pragma unroll
         for (int r = 0; r < PART_ITEMS; ++r) {
-            if (dd[r] < 64) {
+            if (dd[r] < RADIX) {
                 const int pos = (int)(S.dstart[dd[r]] + S.wcnt[w][dd[r]]) + rr[r];
                 S.sk[pos] = kk[r];
                 S.sv[pos] = vv[r];
@@ -901,61 +909,63 @@ __global__ void __launch_bounds__(PART_THREADS, 3)   // three CTAs per SM (the l
             if (dbid) dbid[g] = S.sb[i];
         }
         __syncthreads();
-        for (int i = t; i < (PART_THREADS / 32) * 64; i += PART_THREADS) (&S.wcnt[0][0])[i] = 0;
+        for (int i = t; i < (PART_THREADS / 32) * RADIX; i += PART_THREADS) (&S.wcnt[0][0])[i] = 0;
         __syncthreads();
     }
 }
 
-// Bucket offsets (exclusive scan of the 4096 totals) and bucket statistics.
-__global__ void __launch_bounds__(1024) bucket_offsets_kernel(const unsigned long long* __restrict__ totals,
-                                                              int64_t* __restrict__ off, LearnMeta* meta,
-                                                              float overfull_factor, int64_t n)
+// Bucket offsets from the partitioned bucket ids (non-decreasing after the
+// two stable passes): off[b] = the first position whose bucket is at least b
+// (a lower-bound search per bucket), off[NBUCKETS] = n.  The offsets are
+// non-decreasing and within [0, n] whatever the ids hold.
+__global__ void __launch_bounds__(256) bucket_bounds_kernel(const uint16_t* __restrict__ bid, int64_t n,
+                                                            int64_t* __restrict__ off)
 {
-    __shared__ unsigned long long part[1024];
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > NBUCKETS) return;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((int)bid[mid] < b) lo = mid + 1;
+        else hi = mid;
+    }
+    off[b] = b == NBUCKETS ? n : lo;
+}
+
+// Bucket statistics from the offsets (one CTA).
+__global__ void __launch_bounds__(1024) bucket_stats_kernel(const int64_t* __restrict__ off, LearnMeta* meta,
+                                                            float overfull_factor, int64_t n)
+{
     __shared__ int64_t smax[1024];
     __shared__ int snon[1024], sover[1024];
     constexpr int PER = NBUCKETS / 1024;
     const int t = threadIdx.x;
     const double mean = (double)n / NBUCKETS;
-    unsigned long long sum = 0;
     int64_t mx = 0;
     int non = 0, over = 0;
     for (int k = 0; k < PER; ++k) {
         const int b = t * PER + k;
-        const unsigned long long c = totals[b];
-        sum += c;
-        mx = (int64_t)c > mx ? (int64_t)c : mx;
+        const int64_t c = off[b + 1] - off[b];
+        mx = c > mx ? c : mx;
         non += c > 0;
         over += (double)c > overfull_factor * mean;
     }
-    part[t] = sum;
     smax[t] = mx;
     snon[t] = non;
     sover[t] = over;
     __syncthreads();
     if (t == 0) {
-        unsigned long long run = 0;
         int64_t m = 0;
         int nn = 0, oo = 0;
         for (int q = 0; q < 1024; ++q) {
-            const unsigned long long c = part[q];
-            part[q] = run;
-            run += c;
             m = smax[q] > m ? smax[q] : m;
             nn += snon[q];
             oo += sover[q];
         }
-        off[NBUCKETS] = (int64_t)run;
         meta->max_bucket = m;
         meta->nonempty = nn;
         meta->overfull = oo;
         meta->tied = 0;
-    }
-    __syncthreads();
-    unsigned long long run = part[t];
-    for (int k = 0; k < PER; ++k) {
-        off[t * PER + k] = (int64_t)run;
-        run += totals[t * PER + k];
     }
 }
 
@@ -1112,7 +1122,7 @@ void init_params_host(float* p)
 // rest until the end of the call.
 struct LearnLayout {
     size_t bufk, bufv, bidA, bidB, counts, big;
-    size_t sample, x, t, params, F, spl, spl_raw, table, coarse, uniq, cum, meta, rowtot, btot, diff, tied, off, loss, ctl,
+    size_t sample, x, t, params, F, spl, spl_raw, table, coarse, uniq, cum, meta, rowtot, diff, tied, off, loss, ctl,
         total;
     int64_t ntiles;
 };
@@ -1126,7 +1136,7 @@ LearnLayout learn_layout(int64_t n, bool with_vals)
     o.bufv = off; off += with_vals ? align256((size_t)n * 4) : 0;
     o.bidA = off; off += align256((size_t)n * 2);
     o.bidB = off; off += align256((size_t)n * 2);
-    o.counts = off; off += align256((size_t)64 * (size_t)o.ntiles * 4);
+    o.counts = off; off += align256((size_t)RADIX * (size_t)o.ntiles * 4);
     o.big = off;
     off = 0;
     o.sample = off; off += align256((size_t)SAMPLE_M * 8);
@@ -1141,8 +1151,7 @@ LearnLayout learn_layout(int64_t n, bool with_vals)
     o.cum = off; off += align256((size_t)(NSPLIT + 1) * 2);
     o.spl_raw = off; off += align256((size_t)(NSPLIT + 1) * 8);
     o.meta = off; off += align256(sizeof(LearnMeta));
-    o.rowtot = off; off += align256(64 * 8);
-    o.btot = off; off += align256((size_t)NBUCKETS * 8);
+    o.rowtot = off; off += align256(RADIX * 8);
     o.diff = off; off += align256((size_t)NBUCKETS * 4);
     o.tied = off; off += align256((size_t)NBUCKETS);
     o.off = off; off += align256((size_t)(NBUCKETS + 1) * 8);
@@ -1161,7 +1170,7 @@ struct LearnScratch {
     uint32_t* bufv;
     uint16_t* bidA;
     uint16_t* bidB;
-    uint32_t* counts;   // 64 x ceil(n / PART_TILE)
+    uint32_t* counts;   // RADIX x ceil(n / PART_TILE)
 };
 
 // Phases 1 and 2 of the learned sort into the small workspace `ws`: sample
@@ -1267,7 +1276,6 @@ int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, con
     uint16_t* cum = (uint16_t*)(ws + lay.cum);
     LearnMeta* meta = (LearnMeta*)(ws + lay.meta);
     unsigned long long* rowtot = (unsigned long long*)(ws + lay.rowtot);
-    unsigned long long* btot = (unsigned long long*)(ws + lay.btot);
     uint16_t* bidA = xs ? xs->bidA : (uint16_t*)(big + lay.bidA);
     uint16_t* bidB = xs ? xs->bidB : (uint16_t*)(big + lay.bidB);
     uint8_t* tied = (uint8_t*)(ws + lay.tied);
@@ -1301,30 +1309,32 @@ int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, con
         if (rc != GNS_OK) goto done;
     }
     if (rep) LTRY(cudaEventRecord(ev[1], s));
-    LTRY(cudaMemsetAsync(btot, 0, NBUCKETS * 8, s));
 
     {
-        // pass A: buckets evaluated once (-> bidA), stable scatter by the low 6 bits
-        const int64_t hgrid = imin_h(ntiles, (int64_t)sms * 3);
+        // pass A: buckets evaluated once (-> bidA), stable scatter by the low DIGIT_BITS bits
+        const int64_t hgrid = imin_h(ntiles, (int64_t)sms * 4);
         LTRY(launch(K_LEARN_HIST, part_hist_a_kernel, dim3((unsigned)hgrid), dim3(HIST_THREADS), 0, s,
                     (const uint64_t*)keys, n, mode, (const uint16_t*)table, (const uint32_t*)coarse,
-                    (const uint64_t*)uniq, (const uint16_t*)cum, (const LearnMeta*)meta, bidA, counts, ntiles, btot,
+                    (const uint64_t*)uniq, (const uint16_t*)cum, (const LearnMeta*)meta, bidA, counts, ntiles,
                     fault == GNS_FAULT_BUCKETS_SWAPPED ? 1 : 0));
-        LTRY(launch(K_LEARN_SCAN, row_scan_kernel, dim3(64), dim3(1024), 0, s, counts, ntiles, rowtot));
+        LTRY(launch(K_LEARN_SCAN, row_scan_kernel, dim3(RADIX), dim3(1024), 0, s, counts, ntiles, rowtot));
         const int64_t sgrid = imin_h(ntiles, (int64_t)sms * 3);   // all CTAs resident
         LTRY(launch(K_LEARN_SCATTER, part_scatter_kernel, dim3((unsigned)sgrid), dim3(PART_THREADS), 0, s,
                     (const uint64_t*)keys, (const uint32_t*)vals, (const uint16_t*)bidA, bufk, bufv, bidB, n, 0,
                     (const uint32_t*)counts, ntiles, (const unsigned long long*)rowtot));
-        // pass B: stable scatter by the high 6 bits, back into the caller's arrays
+        // pass B: stable scatter by the high DIGIT_BITS bits, back into the caller's
+        // arrays; the bucket ids land in bidA (free again) for the offsets
         LTRY(launch(K_LEARN_HIST, part_hist_b_kernel, dim3((unsigned)imin_h(ntiles, (int64_t)sms * 8)), dim3(256), 0,
                     s, (const uint16_t*)bidB, n, counts, ntiles));
-        LTRY(launch(K_LEARN_SCAN, row_scan_kernel, dim3(64), dim3(1024), 0, s, counts, ntiles, rowtot));
+        LTRY(launch(K_LEARN_SCAN, row_scan_kernel, dim3(RADIX), dim3(1024), 0, s, counts, ntiles, rowtot));
         LTRY(launch(K_LEARN_SCATTER, part_scatter_kernel, dim3((unsigned)sgrid), dim3(PART_THREADS), 0, s,
-                    (const uint64_t*)bufk, (const uint32_t*)bufv, (const uint16_t*)bidB, keys, vals,
-                    (uint16_t*)nullptr, n, 6, (const uint32_t*)counts, ntiles, (const unsigned long long*)rowtot));
+                    (const uint64_t*)bufk, (const uint32_t*)bufv, (const uint16_t*)bidB, keys, vals, bidA, n,
+                    DIGIT_BITS, (const uint32_t*)counts, ntiles, (const unsigned long long*)rowtot));
     }
-    LTRY(launch(K_LEARN_VERIFY, bucket_offsets_kernel, dim3(1), dim3(1024), 0, s, (const unsigned long long*)btot,
-                boff, meta, prm.overfull_factor, n));
+    LTRY(launch(K_LEARN_VERIFY, bucket_bounds_kernel, dim3(cdiv(NBUCKETS + 1, 256)), dim3(256), 0, s,
+                (const uint16_t*)bidA, n, boff));
+    LTRY(launch(K_LEARN_VERIFY, bucket_stats_kernel, dim3(1), dim3(1024), 0, s, (const int64_t*)boff, meta,
+                prm.overfull_factor, n));
     LTRY(cudaMemsetAsync(diff, 0, NBUCKETS * sizeof(int), s));
     LTRY(launch(K_LEARN_VERIFY, tied_scan_kernel, dim3((unsigned)cdiv(n, TIED_CHUNK)), dim3(256), 0, s,
                 (const uint64_t*)keys, (const int64_t*)boff, (const uint64_t*)spl, diff, n));
@@ -1333,9 +1343,10 @@ int learned_sort_device(uint64_t* keys, uint32_t* vals, int64_t n, int mode, con
     if (rep) LTRY(cudaEventRecord(ev[2], s));
     if (big) ws_free(big, s);
     big = nullptr;
-    // 3. every bucket is a segment
-    rc = segmented_sort_direct(keys, vals, boff, NBUCKETS, n, mode, (const uint8_t*)tied, s, xs ? xs->bufk : nullptr,
-                               xs ? xs->bufv : nullptr);
+    // 3. every bucket is a segment; the buckets are ordered, so the array is
+    // tile-sorted at global tiles and each bucket merged over its own runs
+    rc = ordered_sort_direct(keys, vals, boff, NBUCKETS, n, mode, (const uint8_t*)tied, s, xs ? xs->bufk : nullptr,
+                             xs ? xs->bufv : nullptr);
     if (rc != GNS_OK) goto done;
     // 4. bucket check; where it fails, the plain merge sort re-sorts the whole
     // array (decided on the device: with the check passed its kernels return
@@ -1501,7 +1512,7 @@ bool half_plan(int64_t n, bool with_vals, HalfPlan& P)
         }
         if (cur < total) push_free(cur, total);
         // best fit, largest request first; 256 bytes of slack for the alignment
-        const int64_t req[5] = {8 * L.m, 4 * L.m, 2 * L.m, 2 * L.m, 256 * cdiv(L.m, PART_TILE)};
+        const int64_t req[5] = {8 * L.m, 4 * L.m, 2 * L.m, 2 * L.m, 4 * RADIX * cdiv(L.m, PART_TILE)};
         HalfRegion* to[5] = {&L.bufk, &L.bufv, &L.bidA, &L.bidB, &L.counts};
         for (int r = 0; r < 5; ++r) {
             if (r == 1 && !with_vals) continue;

@@ -258,6 +258,142 @@ __global__ void __launch_bounds__(WS_CONSUMERS + 32, ws_ctas_per_sm<SEG_WS_STAGE
     ws_merge_out<WS_CONSUMERS, WS_ITEMS, SEG_WS_STAGES>(src, vals != nullptr, mode, call_err, limit_ns);
 }
 
+// ---------------------------------------------------------------- ordered segments
+// Segments whose key ranges are ordered (every key of segment s lies at or
+// below every key of segment s + 1, and equal keys share a segment: the
+// learned sort's buckets).  Sorting any range that holds whole parts of
+// several such segments keeps each part in its own positions, so the array is
+// tile-sorted at the global ORD_T-key tiles, each tile sorted whole whatever
+// segment ends it holds, and each segment is finished by merge levels over its
+// own runs.  With a = floor(s0 / ORD_T) * ORD_T for a segment starting at s0,
+// run j covers [a + j ORD_T, a + (j + 1) ORD_T) clipped to the segment (run 0
+// its head inside the first tile, the last its tail); level p merges runs in
+// pairs of 2^p, aligned to a, so the segment needs ceil(log2(tiles it
+// touches)) levels, and chunks of CHUNK outputs aligned to a never straddle
+// a pair.  The data lands in `keys` after a segment's last level (its tiles go
+// to the buffer when its level count is odd).
+constexpr int64_t ORD_T = 8192;
+
+// Largest s in [lo, hi] with off[s] <= pos (off non-decreasing; off[lo] <= pos).
+__device__ __forceinline__ int64_t seg_at(const int64_t* __restrict__ off, int64_t lo, int64_t hi, int64_t pos)
+{
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (__ldg(&off[mid]) <= pos) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Per segment: its level count and, for every level p < L, the chunks it
+// contributes (rows[p * (nseg + 1) + s]).  A segment flagged in skip (all
+// keys equal) or empty gets no level.
+__global__ void ord_count_kernel(const int64_t* __restrict__ off, int64_t nseg, int L, int64_t* rows,
+                                 uint8_t* levels, const uint8_t* __restrict__ skip, const int* ctl)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg || skip_all(ctl)) return;
+    const int64_t stride = nseg + 1;
+    const int64_t s0 = off[s], s1 = off[s + 1];
+    int k = 0;
+    int64_t chunks = 0;
+    if (s1 > s0 && !(skip && skip[s])) {
+        const int64_t a = s0 / ORD_T * ORD_T;
+        const int64_t tiles = (s1 - 1 - a) / ORD_T + 1;
+        while ((1ll << k) < tiles) ++k;
+        chunks = (s1 - 1 - a) / CHUNK - (s0 - a) / CHUNK + 1;
+    }
+    levels[s] = (uint8_t)k;
+    for (int p = 0; p < L; ++p) rows[p * stride + s] = k > p ? chunks : 0;
+}
+
+// One CTA per global tile: the tile is sorted whole, and every output goes to
+// the buffer or to `keys` by its segment's level count (odd: buffer), decoded
+// when the segment has no level.  A tile inside one skipped segment is left
+// as it is.
+template <int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS)   // <= 64 registers: 1024 threads per SM
+    ord_tile_kernel(uint64_t* keys, uint32_t* vals, uint64_t* bufk, uint32_t* bufv, int64_t n,
+                    const int64_t* __restrict__ off, int64_t nseg, const uint8_t* __restrict__ levels,
+                    const uint8_t* __restrict__ skip, int mode, const int* ctl)
+{
+    constexpr int T = THREADS * ITEMS;
+    static_assert(T == ORD_T, "tile");
+    if (skip_all(ctl)) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    SmemKV<T>& sm = *reinterpret_cast<SmemKV<T>*>(smem_raw);
+    __shared__ int64_t s_first, s_last;
+    const int t = threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * T;
+    const int nv = (int)imin64(T, n - base);
+    if (t == 0) {
+        s_first = seg_at(off, 0, nseg - 1, base);
+        s_last = seg_at(off, s_first, nseg - 1, base + nv - 1);
+    }
+    __syncthreads();
+    const int64_t sf = s_first, sl = s_last;
+    if (sf == sl && skip && skip[sf]) return;
+#pragma unroll 4
+    for (int j = 0; j < ITEMS; ++j) {
+        const int e = t + j * THREADS;
+        const bool ok = e < nv;
+        sm.k[pidx(e)] = ok ? encode_key(keys[base + e], mode) : ~0ull;
+        sm.v[pidx(e)] = (ok && vals) ? vals[base + e] : 0u;
+    }
+    block_sort_smem<THREADS, ITEMS>(sm, nv);
+    const int k_one = levels[sf];
+#pragma unroll 4
+    for (int j = 0; j < ITEMS; ++j) {
+        const int e = t + j * THREADS;
+        if (e < nv) {
+            const int k = sf == sl ? k_one : (int)__ldg(&levels[seg_at(off, sf, sl, base + e)]);
+            const uint64_t key = sm.k[pidx(e)];
+            ((k & 1) ? bufk : keys)[base + e] = k == 0 ? decode_key(key, mode) : key;
+            if (vals) ((k & 1) ? bufv : vals)[base + e] = sm.v[pidx(e)];
+        }
+    }
+}
+
+// One thread per work item of level p: its segment, its chunk and both
+// merge-path splits, as absolute positions, written to list[i].
+__global__ void ord_partition_kernel(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ bufk,
+                                     const int64_t* __restrict__ off, int64_t nseg, const int64_t* __restrict__ prefix,
+                                     const uint8_t* __restrict__ levels, int p, SegChunk* list, const int* ctl)
+{
+    if (skip_all(ctl)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= prefix[nseg]) return;
+    const int64_t s = seg_of(prefix, nseg, i);
+    const int64_t s0 = off[s], s1 = off[s + 1];
+    const int64_t a = s0 / ORD_T * ORD_T;
+    const int k = levels[s];
+    const int from_buf = (k - p) & 1;
+    const uint64_t* src = from_buf ? bufk : keys;
+    const int64_t w = ORD_T << p;
+    const int64_t c = (s0 - a) / CHUNK + (i - prefix[s]);      // chunk index counted from a
+    const int64_t o0 = imax64(s0, a + c * CHUNK), o1 = imin64(s1, a + (c + 1) * CHUNK);
+    const int64_t pair_lo = a + (c * CHUNK) / (2 * w) * (2 * w), pair_mid = pair_lo + w, pair_hi = pair_mid + w;
+    const int64_t pa0 = imax64(s0, pair_lo), pa1 = imin64(s1, pair_mid);
+    const int64_t pb0 = imin64(imax64(s0, pair_mid), s1), pb1 = imin64(s1, pair_hi);   // empty B: at s1
+    const int64_t lenA = imax64(0, pa1 - pa0), lenB = imax64(0, pb1 - pb0);
+    const int64_t d0 = o0 - pa0, d1 = o1 - pa0;                 // the pair's outputs start at pa0
+    const uint64_t* A = src + pa0;
+    const uint64_t* B = src + pb0;
+    auto ga = [&](int64_t x) { return A[x]; };
+    auto gb = [&](int64_t x) { return B[x]; };
+    const int64_t a0 = merge_path(d0, lenA, lenB, ga, gb);
+    const int64_t a1 = merge_path(d1, lenA, lenB, ga, gb);
+    SegChunk r;
+    r.out0 = o0;
+    r.a_src = pa0 + a0;
+    r.b_src = pb0 + (d0 - a0);
+    r.na = (int32_t)(a1 - a0);
+    r.nb = (int32_t)((d1 - a1) - (d0 - a0));
+    r.flags = from_buf | ((p == k - 1) ? 2 : 0);
+    r.pad = 0;
+    list[i] = r;
+}
+
 // ---------------------------------------------------------------- host side
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -327,6 +463,8 @@ void seg_init_attributes()
                              (int)sizeof(SmemKV<1024>));
         cudaFuncSetAttribute(seg_merge_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(WsSmemOut<WS_CHUNK, SEG_WS_STAGES>));
+        cudaFuncSetAttribute(ord_tile_kernel<512, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(SmemKV<8192>));
     });
 }
 
@@ -377,6 +515,50 @@ cudaError_t seg_enqueue(uint64_t* keys, uint32_t* vals, const int64_t* off, int6
         e = launch(K_SEG_MERGE, seg_partition_kernel, dim3((unsigned)ceil_div(lay.max_items, 256)), dim3(256), 0, s,
                    (const uint64_t*)keys, (const uint64_t*)bufk, off, nseg, prefix, (const uint8_t*)levels, p,
                    (int64_t)sch.big_t, list, (const int*)ctl);
+        if (e != cudaSuccess) return e;
+        const int64_t cap = (int64_t)sms * ws_ctas_per_sm<SEG_WS_STAGES>();
+        const int64_t grid = lay.max_items < cap ? lay.max_items : cap;
+        e = launch(K_SEG_MERGE, seg_merge_ws_kernel, dim3((unsigned)grid), dim3(WS_CONSUMERS + 32),
+                   sizeof(WsSmemOut<WS_CHUNK, SEG_WS_STAGES>), s, keys, vals, bufk, bufv, n, (const SegChunk*)list,
+                   (const int64_t*)(prefix + nseg), mode, call_err, wait_limit_ns(), (const int*)ctl);
+        if (e != cudaSuccess) return e;
+    }
+    return publish_call_error(call_err, s);
+}
+
+// Enqueues the sort of ordered segments on s (keys/vals in place, ws laid out
+// by seg_layout; rows 0 .. L-1 of it hold the level rows).
+cudaError_t ord_enqueue(uint64_t* keys, uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, int mode,
+                        char* ws, const SegLayout& lay, cudaStream_t s, const uint8_t* skip, uint64_t* xbufk,
+                        uint32_t* xbufv)
+{
+    int* ctl = (int*)(ws + lay.ctl);
+    int* call_err = ctl + 2;
+    uint64_t* bufk = xbufk ? xbufk : (uint64_t*)(ws + lay.bufk);
+    uint32_t* bufv = vals ? (xbufk ? xbufv : (uint32_t*)(ws + lay.bufv)) : nullptr;
+    int64_t* rows = (int64_t*)(ws + lay.rows);
+    uint8_t* levels = (uint8_t*)(ws + lay.levels);
+    SegChunk* list = (SegChunk*)(ws + lay.list);
+    const int64_t stride = nseg + 1;
+    const int sms = num_sms_dev();
+    cudaError_t e = cudaMemsetAsync(ctl, 0, 256, s);
+    if (e != cudaSuccess) return e;
+    e = launch(K_SEG_PLAN, ord_count_kernel, dim3((unsigned)ceil_div(nseg, 256)), dim3(256), 0, s, off, nseg, lay.L,
+               rows, levels, skip, (const int*)ctl);
+    if (e != cudaSuccess) return e;
+    if (lay.L > 0) {
+        e = launch(K_SEG_PLAN, seg_scan_kernel, dim3((unsigned)lay.L), dim3(1024), 0, s, rows, nseg, (const int*)ctl);
+        if (e != cudaSuccess) return e;
+    }
+    e = launch(K_SEG_TILE, ord_tile_kernel<512, 16>, dim3((unsigned)ceil_div(n, ORD_T)), dim3(512),
+               sizeof(SmemKV<8192>), s, keys, vals, bufk, bufv, n, off, nseg, (const uint8_t*)levels, skip, mode,
+               (const int*)ctl);
+    if (e != cudaSuccess) return e;
+    for (int p = 0; p < lay.L; ++p) {
+        const int64_t* prefix = rows + p * stride;
+        e = launch(K_SEG_MERGE, ord_partition_kernel, dim3((unsigned)ceil_div(lay.max_items, 256)), dim3(256), 0, s,
+                   (const uint64_t*)keys, (const uint64_t*)bufk, off, nseg, prefix, (const uint8_t*)levels, p, list,
+                   (const int*)ctl);
         if (e != cudaSuccess) return e;
         const int64_t cap = (int64_t)sms * ws_ctas_per_sm<SEG_WS_STAGES>();
         const int64_t grid = lay.max_items < cap ? lay.max_items : cap;
@@ -571,6 +753,25 @@ int segmented_sort_direct(uint64_t* keys, uint32_t* vals, const int64_t* off, in
     char* ws = (char*)ws_alloc(lay.total, s);
     if (!ws) return GNS_ERR_OOM;
     cudaError_t e = seg_enqueue(keys, vals, off, nseg, n, mode, kDirect, ws, lay, s, skip, ext ? xbufk : nullptr,
+                                ext ? xbufv : nullptr);
+    ws_free(ws, s);
+    return e == cudaSuccess ? GNS_OK : GNS_ERR_CUDA;
+}
+
+
+// Sort of ordered segments (see ord_count_kernel): the learned sort's buckets.
+// Same arguments and results as segmented_sort_direct; the segments must be
+// ordered, which the bucket check after the call verifies.
+int ordered_sort_direct(uint64_t* keys, uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, int mode,
+                        const uint8_t* skip, cudaStream_t s, uint64_t* xbufk, uint32_t* xbufv)
+{
+    if (nseg == 0 || n <= 1) return GNS_OK;
+    seg_init_attributes();
+    const bool ext = xbufk != nullptr && (vals == nullptr || xbufv != nullptr);
+    const SegLayout lay = seg_layout(n, nseg, vals != nullptr, ext);
+    char* ws = (char*)ws_alloc(lay.total, s);
+    if (!ws) return GNS_ERR_OOM;
+    cudaError_t e = ord_enqueue(keys, vals, off, nseg, n, mode, ws, lay, s, skip, ext ? xbufk : nullptr,
                                 ext ? xbufv : nullptr);
     ws_free(ws, s);
     return e == cudaSuccess ? GNS_OK : GNS_ERR_CUDA;
