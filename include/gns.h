@@ -445,6 +445,20 @@ void gns_debug_skip_publish(int64_t ticket);
  * until reset. */
 void gns_debug_jitter(uint32_t max_ns);
 
+/* Test hook: the learned sort's bucket sort on its own -- a stable sort of
+ * ordered segments.  keys: device, n float64 or int64 keys (key_type) in
+ * place; payload: device uint32[n] or NULL; offsets: device int64[nseg + 1],
+ * offsets[0] == 0, non-decreasing, offsets[nseg] == n (not validated on the
+ * device).  The segments must be ordered under `order`: every key of segment
+ * s at or before every key of segment s + 1, equal keys in one segment (the
+ * result is undefined otherwise).  The array is tile-sorted at its global
+ * 8192-key tiles, each tile sorted whole whatever segment ends it holds, and
+ * every segment spanning tiles is finished by merge levels over its own runs;
+ * the result is the stable sort of the whole array.  Returns GNS_OK,
+ * GNS_ERR_INVALID, GNS_ERR_OOM or GNS_ERR_CUDA. */
+int gns_debug_ordered_segments(void* keys, int key_type, uint32_t* payload, int64_t n, const int64_t* offsets,
+                               int64_t nseg, int order, gns_stream_t stream);
+
 /* Test hook: the merge-path partition of one Nocopy merge level ("Parallel"
  * section) on its own.  keys: device, n order-mapped 64-bit keys whose
  * consecutive runs of w keys are sorted (w a multiple of 1024); splits:

@@ -14,5 +14,6 @@ from ._native import (ASCENDING, DESCENDING, GNS_ERR_CUDA, GNS_ERR_INVALID, GNS_
                       FROGSORT1, GECKOSORT1, SQUIDSORT1, gns_stream_status, gns_version,
                       gns_learned_sort, gns_learned_half_plan_ok, gns_mlp_forward, gns_mlp_init_params, gns_mlp_loss_grad, gns_mlp_train,
                       gns_workspace_bytes, gns_release_workspace_cache, GNS_ERR_INTERNAL, strerror, lib,
-                      gns_debug_learned_fault, gns_debug_jitter, gns_debug_merge_partition, FAULT_NONE, FAULT_BUCKETS_SWAPPED,
+                      gns_debug_learned_fault, gns_debug_jitter, gns_debug_merge_partition,
+                      gns_debug_ordered_segments, FAULT_NONE, FAULT_BUCKETS_SWAPPED,
                       FAULT_GARBAGE_WEIGHTS, FAULT_SPLITTERS_REVERSED)

@@ -75,6 +75,7 @@ def lib() -> ctypes.CDLL:
                 "gns_debug_learned_fault": ([i32], None),
                 "gns_debug_jitter": ([ctypes.c_uint32], None),
                 "gns_debug_merge_partition": ([P, i64, i64, P, P], i32),
+                "gns_debug_ordered_segments": ([P, i32, P, i64, P, i64, i32, P], i32),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -337,6 +338,22 @@ def gns_debug_learned_fault(kind: int) -> None:
 def gns_debug_jitter(max_ns: int) -> None:
     """Test hook: perturb the load order of the in-place levels' tickets."""
     lib().gns_debug_jitter(int(max_ns))
+
+
+def gns_debug_ordered_segments(keys, payload, offsets, order: int = ASCENDING, stream=None) -> None:
+    """Test hook: the learned sort's bucket sort on caller-given ordered
+    segments (offsets: CUDA int64 tensor of nseg + 1 entries)."""
+    import torch
+    if keys.dtype == torch.int64:
+        kt = KEY_I64
+    elif keys.dtype == torch.float64:
+        kt = KEY_F64
+    else:
+        raise TypeError("keys must be int64 or float64")
+    _check(lib().gns_debug_ordered_segments(_dev_ptr(keys, keys.dtype, "keys"), kt,
+                                            _dev_ptr(payload, torch.int32, "payload"), keys.numel(),
+                                            _dev_ptr(offsets, torch.int64, "offsets"), offsets.numel() - 1,
+                                            order, _stream(stream)), "gns_debug_ordered_segments")
 
 
 def gns_debug_merge_partition(keys, w: int, stream=None):

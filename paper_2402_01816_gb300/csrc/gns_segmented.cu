@@ -821,6 +821,21 @@ int gns_segmented_sort_ex(void* keys, int key_type, uint32_t* payload, const int
     return finish_call(rc, s);
 }
 
+int gns_debug_ordered_segments(void* keys, int key_type, uint32_t* payload, int64_t n, const int64_t* offsets,
+                               int64_t nseg, int order, gns_stream_t stream)
+{
+    if (nseg < 1 || n < 0 || offsets == nullptr) return GNS_ERR_INVALID;
+    if (key_type != GNS_KEY_F64 && key_type != GNS_KEY_I64) return GNS_ERR_INVALID;
+    if (order != GNS_ASCENDING && order != GNS_DESCENDING) return GNS_ERR_INVALID;
+    if (n > 0 && keys == nullptr) return GNS_ERR_INVALID;
+    if (((uintptr_t)keys & 7) || ((uintptr_t)payload & 3) || ((uintptr_t)offsets & 7)) return GNS_ERR_INVALID;
+    if (nseg > 0x7fffffff) return GNS_ERR_UNSUPPORTED;
+    const int mode = (key_type == GNS_KEY_I64 ? MODE_I64 : 0) | (order == GNS_DESCENDING ? MODE_DESC : 0);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int rc = ordered_sort_direct((uint64_t*)keys, payload, offsets, nseg, n, mode, nullptr, s);
+    return finish_call(rc, s);
+}
+
 int gns_segmented_sort(int64_t* keys, uint32_t* payload, const int64_t* offsets, int64_t nseg, gns_stream_t stream)
 {
     if (nseg < 0) return GNS_ERR_INVALID;

@@ -217,3 +217,18 @@ def test_symmetric_host_argument_checks(L, args, code):
 def test_symmetric_trivial_sizes_are_no_ops(L):
     assert L.gns_sort_symmetric(None, 0, None, 0, 0, 0.5, 2, None) == 0
     assert L.gns_sort_symmetric(FAKE, 1, None, 1, 1, 0.25, 1, None) == 0
+
+
+@pytest.mark.parametrize("args", [
+    (FAKE, 0, None, 10, FAKE, 0, 0),                      # no segment
+    (FAKE, 0, None, 10, None, 2, 0),                      # NULL offsets
+    (FAKE, 2, None, 10, FAKE, 2, 0),                      # unknown key type
+    (FAKE, 0, None, 10, FAKE, 2, 2),                      # unknown order
+    (FAKE, 0, None, -1, FAKE, 2, 0),                      # n < 0
+    (None, 0, None, 10, FAKE, 2, 0),                      # NULL keys with n > 0
+    (FAKE + 4, 0, None, 10, FAKE, 2, 0),                  # keys not 8-byte aligned
+    (FAKE, 0, FAKE + 2, 10, FAKE, 2, 0),                  # payload not 4-byte aligned
+    (FAKE, 0, None, 10, FAKE + 4, 2, 0),                  # offsets not 8-byte aligned
+])
+def test_ordered_segments_host_argument_checks(L, args):
+    assert L.gns_debug_ordered_segments(*args, None) == -1
