@@ -129,9 +129,9 @@ struct FrogItem {
     int64_t ra, rb;        // lowest slot of the first / second slice (left / right run unless SYM)
     int64_t oslot;         // slot of the first output
     int32_t na, nb;        // slice lengths (0, 0: nothing to do)
-    int32_t dep_lo, dep_hi;   // tickets whose loads must precede the store (dep_hi < dep_lo: none)
+    int32_t dep_lo, dep_hi;   // items whose loads must precede the store (dep_hi < dep_lo: none)
     int32_t flags;         // SYM levels: FI_REV_A / FI_REV_B (slice read from its far end), FI_DESC
-    int32_t pad;
+    int32_t id;            // the item's "loaded" flag: node-major, node k's items at base(k) + local
 };
 enum { FI_REV_A = 1, FI_REV_B = 2, FI_DESC = 4 };
 
@@ -251,8 +251,17 @@ __device__ __forceinline__ int2 frog_dep_range_sym(int64_t c, const FrogNode& x,
 }
 
 // items[tk] for every ticket tk of a level (after the partition, before the
-// merge): ticket tk = base(k) + local (frog_locate) is chunk c = nchk - 1 -
-// local of a data-left node k and chunk c = local of a data-right one.
+// merge).  An item is chunk c = nchk - 1 - local of a data-left node k or
+// chunk c = local of a data-right one; its flag is id = base(k) + local
+// (node-major, as frog_locate numbers them), and the dependency ranges are ids.
+// Tickets hand the items out interleaved across the nodes when every node has
+// nch chunk slots (the Frogsort1 tree): ticket tk is local = tk / nnodes of
+// node k = tk mod nnodes.  Within a node the locals still come in increasing
+// ticket order, so every item a store waits on holds an earlier ticket (no
+// cycle of waits), and consecutive items of one node lie nnodes tickets
+// apart: on a level of many small nodes a store no longer waits on a ticket
+// taken just before its own.  A host-planned tree (cstart, nodes of unequal
+// chunk counts) keeps node-major tickets.
 //
 // skip_identity: a chunk whose outputs all come from one run and already sit
 // in their output slots (the leading left-run chunks of a data-left node, the
@@ -271,7 +280,14 @@ __global__ void frog_items_kernel(const FrogNode* __restrict__ level, const Frog
     const int64_t tk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (tk >= total || skip_all(presorted)) return;
     int64_t k, local, base, nchk;
-    frog_locate(tk, cstart, nnodes, nch, k, local, base, nchk);
+    if (cstart) {
+        frog_locate(tk, cstart, nnodes, nch, k, local, base, nchk);
+    } else {
+        local = tk / nnodes;
+        k = tk - local * nnodes;
+        base = k * nch;
+        nchk = nch;
+    }
     const FrogNode x = level[k];
     const int64_t c = x.side == 0 ? nchk - 1 - local : local;
     FrogItem it;
@@ -280,7 +296,7 @@ __global__ void frog_items_kernel(const FrogNode* __restrict__ level, const Frog
     it.dep_lo = 0;
     it.dep_hi = -1;
     it.flags = 0;
-    it.pad = 0;
+    it.id = (int32_t)(base + local);
     const int64_t w0 = c * CHUNK;
     if (w0 < x.n) {
         const int64_t w1 = imin64(w0 + CHUNK, x.n);

@@ -822,7 +822,7 @@ struct FrogLevelSrc {
         L.dv = contiguous && hv ? sl.vp(o) : nullptr;
         L.oslot = o;
         L.decode = decode;
-        L.tk = tk;
+        L.tk = it.id;                 // the item's flag (node-major id)
         L.dep_lo = it.dep_lo;
         L.dep_hi = it.dep_hi;
         L.flags = it.flags;
