@@ -254,14 +254,18 @@ __device__ __forceinline__ int2 frog_dep_range_sym(int64_t c, const FrogNode& x,
 // merge).  An item is chunk c = nchk - 1 - local of a data-left node k or
 // chunk c = local of a data-right one; its flag is id = base(k) + local
 // (node-major, as frog_locate numbers them), and the dependency ranges are ids.
-// Tickets hand the items out interleaved across the nodes when every node has
-// nch chunk slots (the Frogsort1 tree): ticket tk is local = tk / nnodes of
-// node k = tk mod nnodes.  Within a node the locals still come in increasing
-// ticket order, so every item a store waits on holds an earlier ticket (no
-// cycle of waits), and consecutive items of one node lie nnodes tickets
-// apart: on a level of many small nodes a store no longer waits on a ticket
-// taken just before its own.  A host-planned tree (cstart, nodes of unequal
-// chunk counts) keeps node-major tickets.
+// Tickets hand the items out interleaved across the nodes: round j takes
+// position j of every node that has more than j chunks.  When every node has
+// nch chunk slots (the Frogsort1 tree) ticket tk is local = tk / nnodes of
+// node k = tk mod nnodes.  A host-planned tree (cstart: nodes of unequal
+// chunk counts) lists each depth's nodes largest first, and iseg holds the
+// runs of rounds with one node count as triples (first ticket, first round,
+// nodes per round): ticket tk of run t is round j = j_t + (tk - ts_t) / c_t of
+// node (tk - ts_t) mod c_t.  Within a node the locals
+// come in increasing ticket order, so every item a store waits on holds an
+// earlier ticket (no cycle of waits), and consecutive items of one node lie
+// a round apart: on a level of many small nodes a store no longer waits on a
+// ticket taken just before its own.
 //
 // skip_identity: a chunk whose outputs all come from one run and already sit
 // in their output slots (the leading left-run chunks of a data-left node, the
@@ -275,13 +279,24 @@ template <bool SYM>
 __global__ void frog_items_kernel(const FrogNode* __restrict__ level, const FrogNode* __restrict__ child,
                                   int64_t nnodes, int64_t nch, const int64_t* __restrict__ cstart, int64_t total,
                                   const int64_t* __restrict__ splits, FrogItem* __restrict__ items, int* call_err,
-                                  const int* presorted, int skip_identity)
+                                  const int* presorted, int skip_identity, const int32_t* __restrict__ iseg,
+                                  int64_t nseg)
 {
     const int64_t tk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (tk >= total || skip_all(presorted)) return;
     int64_t k, local, base, nchk;
     if (cstart) {
-        frog_locate(tk, cstart, nnodes, nch, k, local, base, nchk);
+        int64_t lo = 0, hi = nseg - 1;                  // last run t with ts_t <= tk
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (iseg[3 * mid] <= tk) lo = mid;
+            else hi = mid - 1;
+        }
+        const int64_t off = tk - iseg[3 * lo], cnt = iseg[3 * lo + 2];
+        local = iseg[3 * lo + 1] + off / cnt;
+        k = off % cnt;
+        base = cstart[k];
+        nchk = cstart[k + 1] - base;
     } else {
         local = tk / nnodes;
         k = tk - local * nnodes;

@@ -85,6 +85,14 @@ void frog2_split(const FrogNode& p, int64_t pn, FrogNode& L, FrogNode& R)
 struct Frog2Plan {
     std::vector<FrogNode> internal, children, leaves;
     std::vector<int64_t> cstart, first_node, first_cs;
+    // Ticket order of each depth, interleaved across its nodes (frog_items_kernel):
+    // round j hands out chunk position j of every node holding more than j
+    // chunks.  Each depth's nodes are listed largest first, so the nodes of a
+    // round are a prefix of the list; iseg holds, from first_sg[d] on, triples
+    // (first ticket, first round, nodes per round) of the runs of rounds with
+    // one node count.
+    std::vector<int32_t> iseg;
+    std::vector<int64_t> first_sg;
     // index into `leaves` of the outermost leaf of internal[i] (i < #internal)
     // and of children[j] (at #internal + j): a node of a symmetric variant
     // takes that leaf's orientation (frog_orient_kernel)
@@ -100,6 +108,8 @@ Frog2Plan frog2_plan(int64_t n, int64_t pn)
     cur[0].n = n; cur[0].b = n * pn / FROG2_DEN; cur[0].r = 0; cur[0].s = 0; cur[0].side = 0; cur[0].ori = 0;
     while (!cur.empty()) {
         nxt.clear();
+        // largest first: the interleaved ticket order takes a prefix of the list
+        std::stable_sort(cur.begin(), cur.end(), [](const FrogNode& a, const FrogNode& b) { return a.n > b.n; });
         const int64_t first = (int64_t)P.internal.size(), first_c = (int64_t)P.cstart.size();
         int64_t acc = 0;
         for (const FrogNode& x : cur) {
@@ -119,6 +129,24 @@ Frog2Plan frog2_plan(int64_t n, int64_t pn)
         }
         if ((int64_t)P.internal.size() == first) break;
         P.cstart.push_back(acc);
+        {
+            const int64_t nk = (int64_t)P.internal.size() - first;
+            auto chunks = [&](int64_t k) { return P.cstart[first_c + k + 1] - P.cstart[first_c + k]; };
+            P.first_sg.push_back((int64_t)P.iseg.size() / 3);
+            // rounds [v, v') with v, v' consecutive distinct chunk counts (from 0
+            // up) have the same nodes: those whose count reaches v'
+            int64_t ts = 0, v = 0;
+            for (int64_t i = nk - 1; i >= 0; --i) {
+                const int64_t m = chunks(i);
+                if (m <= v) continue;
+                const int64_t cnt = i + 1;              // nodes with count >= m (listed largest first)
+                P.iseg.push_back((int32_t)ts);         // a depth has fewer than 2^31 chunks
+                P.iseg.push_back((int32_t)v);
+                P.iseg.push_back((int32_t)cnt);
+                ts += cnt * (m - v);
+                v = m;
+            }
+        }
         P.first_node.push_back(first);
         P.first_cs.push_back(first_c);
         P.max_items = acc > P.max_items ? acc : P.max_items;
@@ -126,6 +154,7 @@ Frog2Plan frog2_plan(int64_t n, int64_t pn)
         cur.swap(nxt);
     }
     P.first_node.push_back((int64_t)P.internal.size());
+    P.first_sg.push_back((int64_t)P.iseg.size() / 3);
     std::sort(P.leaves.begin(), P.leaves.end(), [](const FrogNode& a, const FrogNode& b) { return a.s < b.s; });
     // outermost leaf: a data-left node's leftmost leaf (the one starting at its
     // first element), a data-right node's rightmost (the one holding its last)
@@ -151,8 +180,8 @@ struct Frog2Dev {
     int dev = -1;
     int64_t n = 0, pn = 0;
     Frog2Plan plan;               // host copy: per-depth offsets and totals
-    char* d = nullptr;            // internal | children | leaves | cstart | outer_leaf
-    size_t o_ch = 0, o_lv = 0, o_cs = 0, o_ol = 0;
+    char* d = nullptr;            // internal | children | leaves | cstart | iseg | outer_leaf
+    size_t o_ch = 0, o_lv = 0, o_cs = 0, o_sg = 0, o_ol = 0;
     uint64_t used = 0;
 };
 std::mutex g_frog2_mu;
@@ -178,13 +207,15 @@ const Frog2Dev* frog2_get(int64_t n, int64_t pn)
     e.o_ch = P.internal.size() * sizeof(FrogNode);
     e.o_lv = e.o_ch + P.children.size() * sizeof(FrogNode);
     e.o_cs = e.o_lv + P.leaves.size() * sizeof(FrogNode);
-    e.o_ol = e.o_cs + P.cstart.size() * sizeof(int64_t);
+    e.o_sg = e.o_cs + P.cstart.size() * sizeof(int64_t);
+    e.o_ol = e.o_sg + P.iseg.size() * sizeof(int32_t);
     const size_t bytes = e.o_ol + P.outer_leaf.size() * sizeof(int32_t);
     std::vector<char> blob(bytes);
     if (!P.internal.empty()) memcpy(blob.data(), P.internal.data(), e.o_ch);
     if (!P.children.empty()) memcpy(blob.data() + e.o_ch, P.children.data(), e.o_lv - e.o_ch);
     if (!P.leaves.empty()) memcpy(blob.data() + e.o_lv, P.leaves.data(), e.o_cs - e.o_lv);
-    if (!P.cstart.empty()) memcpy(blob.data() + e.o_cs, P.cstart.data(), e.o_ol - e.o_cs);
+    if (!P.cstart.empty()) memcpy(blob.data() + e.o_cs, P.cstart.data(), e.o_sg - e.o_cs);
+    if (!P.iseg.empty()) memcpy(blob.data() + e.o_sg, P.iseg.data(), e.o_ol - e.o_sg);
     if (!P.outer_leaf.empty()) memcpy(blob.data() + e.o_ol, P.outer_leaf.data(), bytes - e.o_ol);
     if (cudaMalloc(&e.d, bytes ? bytes : 16) != cudaSuccess) {
         cudaGetLastError();
@@ -438,7 +469,8 @@ size_t sort_workspace_bytes(int64_t n, double bf)
         const Frog2Plan plan = frog2_plan(n, frog2_num(bf));
         // the plan itself is kept by the library (frog2_get), apart from the workspace
         const size_t plan_bytes = (plan.internal.size() + plan.children.size() + plan.leaves.size()) *
-                                      sizeof(FrogNode) + plan.cstart.size() * sizeof(int64_t);
+                                      sizeof(FrogNode) + plan.cstart.size() * sizeof(int64_t) +
+                                  (plan.outer_leaf.size() + plan.iseg.size()) * sizeof(int32_t);
         return make_layout(n, bf, true, &plan).total + align256(plan_bytes);
     }
     return make_layout(n, bf, true, nullptr).total;
@@ -592,19 +624,21 @@ int sort_device_variant(uint64_t* keys, uint32_t* vals, int64_t n, int mode, dou
             const FrogNode* level = internal + f0;
             const FrogNode* child = children + 2 * f0;
             const int64_t* cs = cstart + c0;
+            const int32_t* sg = (const int32_t*)(fp->d + fp->o_sg) + 3 * plan.first_sg[d];
+            const int64_t nsg = plan.first_sg[d + 1] - plan.first_sg[d];
             const dim3 pgrid((unsigned)ceil_div(total, 256));
             if (sym) {
                 GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel<true>, pgrid, dim3(256), 0, s, sl, level,
                                child, nnodes, (int64_t)0, cs, total, splits, skip));
                 GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel<true>, pgrid, dim3(256), 0, s, level, child,
                                nnodes, (int64_t)0, cs, total, (const int64_t*)splits, items, call_err, skip,
-                               (int)(d != 0)));
+                               (int)(d != 0), sg, nsg));
             } else {
                 GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel<false>, pgrid, dim3(256), 0, s, sl, level,
                                child, nnodes, (int64_t)0, cs, total, splits, skip));
                 GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel<false>, pgrid, dim3(256), 0, s, level, child,
                                nnodes, (int64_t)0, cs, total, (const int64_t*)splits, items, call_err, skip,
-                               (int)(d != 0)));
+                               (int)(d != 0), sg, nsg));
             }
             GNS_TRY(launch_frog_level(sl, (const FrogItem*)items, total, mode, (int)(d == 0), tickets + d, lflags,
                                       D - d, call_err, limit, skip_ticket, skip, s, sym));
@@ -661,13 +695,15 @@ int sort_device_variant(uint64_t* keys, uint32_t* vals, int64_t n, int mode, dou
                                child, nnodes, nch, (const int64_t*)nullptr, nnodes * nch, splits, skip));
                 GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel<true>, pgrid, dim3(256), 0, s, level, child,
                                nnodes, nch, (const int64_t*)nullptr, nnodes * nch, (const int64_t*)splits, items,
-                               call_err, skip, (int)(d != 0)));
+                               call_err, skip, (int)(d != 0), (const int32_t*)nullptr,
+                               (int64_t)0));
             } else {
                 GNS_TRY(launch(K_FROG_PARTITION, frog_partition_kernel<false>, pgrid, dim3(256), 0, s, sl, level,
                                child, nnodes, nch, (const int64_t*)nullptr, nnodes * nch, splits, skip));
                 GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel<false>, pgrid, dim3(256), 0, s, level, child,
                                nnodes, nch, (const int64_t*)nullptr, nnodes * nch, (const int64_t*)splits, items,
-                               call_err, skip, (int)(d != 0)));
+                               call_err, skip, (int)(d != 0), (const int32_t*)nullptr,
+                               (int64_t)0));
             }
             GNS_TRY(launch_frog_level(sl, (const FrogItem*)items, nnodes * nch, mode, (int)(d == 0), tickets + d,
                                       lflags, D - d, call_err, limit, skip_ticket, skip, s, sym));
@@ -726,7 +762,7 @@ int frog_levels_device(const Slots& sl, const FrogNode* nodes, int D, int mode, 
                        skip));
         GNS_TRY(launch(K_FROG_PARTITION, frog_items_kernel<false>, dim3((unsigned)ceil_div(nnodes * nch, 256)), dim3(256), 0,
                        s, level, child, nnodes, nch, (const int64_t*)nullptr, nnodes * nch, (const int64_t*)splits,
-                       items, call_err, skip, (int)(d != 0)));
+                       items, call_err, skip, (int)(d != 0), (const int32_t*)nullptr, (int64_t)0));
         GNS_TRY(launch_frog_level(sl, (const FrogItem*)items, nnodes * nch, mode, (int)(d == 0), tickets + d, flags,
                                   D - d, call_err, limit, (int64_t)-1, skip, s));
     }
@@ -749,7 +785,10 @@ done:
 //   4  the leaves, in input order, cover [0, n) without gaps and hold at most
 //      one tile each;
 //   5  every data slot range lies inside the slots [0, n + b);
-//   6  chunk numbering: each depth's node chunks are numbered consecutively.
+//   6  chunk numbering: each depth's node chunks are numbered consecutively;
+//   7  ticket order (Frogsort2): each depth's tickets map one to one onto its
+//      chunks (frog_items_kernel's mapping from iseg), and within a
+//      node the chunk positions come in increasing ticket order.
 namespace gns {
 namespace {
 
@@ -798,6 +837,29 @@ extern "C" int gns_frog_plan_check(int64_t n, double buffer_fraction)
             if (P.cstart[c0] != 0) return 6;
             for (int64_t k = 0; k < nn; ++k)
                 if (P.cstart[c0 + k + 1] - P.cstart[c0 + k] != ceil_div(P.internal[f0 + k].n, CHUNK)) return 6;
+            // the device's ticket -> (node, position) mapping, ticket by ticket
+            const int64_t tot = P.cstart[c0 + nn], g0 = P.first_sg[d], ns = P.first_sg[d + 1] - g0;
+            if (ns < 1) return 7;
+            std::vector<char> seen((size_t)tot, 0);
+            std::vector<int64_t> next_pos((size_t)nn, 0);
+            for (int64_t tk = 0; tk < tot; ++tk) {
+                int64_t lo = 0, hi = ns - 1;
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi + 1) >> 1;
+                    if (P.iseg[3 * (g0 + mid)] <= tk) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int64_t off = tk - P.iseg[3 * (g0 + lo)], cnt = P.iseg[3 * (g0 + lo) + 2];
+                if (off < 0 || cnt < 1 || cnt > nn) return 7;
+                const int64_t local = P.iseg[3 * (g0 + lo) + 1] + off / cnt;
+                const int64_t k = off % cnt;
+                if (k < 0 || k >= nn) return 7;
+                const int64_t base = P.cstart[c0 + k], nchk = P.cstart[c0 + k + 1] - base;
+                if (local < 0 || local >= nchk || seen[(size_t)(base + local)]) return 7;
+                seen[(size_t)(base + local)] = 1;
+                if (local < next_pos[(size_t)k]) return 7;            // positions of a node in ticket order
+                next_pos[(size_t)k] = local + 1;
+            }
         }
         return check_leaves(P.leaves, n, total);
     }

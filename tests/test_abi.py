@@ -153,8 +153,10 @@ def test_frog_plan_invariants(L, bf):
     split (Frogsort1) and planner (Frogsort2): children split each node
     exactly, every node can hold its inner child in its buffer, the leaves
     tile the input in order, every data slot lies in the n + buffer slots,
-    chunk numbering is consecutive.  Sizes near tile multiples, odd sizes,
-    and up to 2^31."""
+    chunk numbering is consecutive, and (Frogsort2) the interleaved ticket
+    order maps one to one onto each depth's chunks with every node's chunk
+    positions in ticket order.  Sizes near tile multiples, odd sizes, and up
+    to 2^31."""
     import random
     L.gns_frog_plan_check.argtypes = [ctypes.c_int64, ctypes.c_double]
     L.gns_frog_plan_check.restype = ctypes.c_int

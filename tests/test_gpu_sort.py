@@ -164,7 +164,7 @@ def test_frogsort2_workspace_is_p_of_data():
     n = 1 << 22
     for p in (0.25, 0.1):
         ws = g.gns_workspace_bytes(n, p)
-        assert 12 * p * n <= ws < 12 * p * n + 0.1 * n     # %RAM = 1 + p + under 1%
+        assert 12 * p * n <= ws < 12 * p * n + 0.12 * n    # %RAM = 1 + p + under 1% (0.12 n of 12 n bytes)
 
 
 @pytest.mark.parametrize("bf", TIERS)
