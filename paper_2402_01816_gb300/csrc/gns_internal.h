@@ -138,9 +138,6 @@ size_t sort_workspace_bytes(int64_t n, double buffer_fraction);
 int segmented_sort_device(uint64_t* keys, uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, int mode,
                           cudaStream_t s);
 size_t segmented_workspace_bytes(int64_t n, int64_t nseg, bool ext_buf = false);
-int segmented_sort_direct(uint64_t* keys, uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, int mode,
-                          const uint8_t* skip, cudaStream_t s, uint64_t* xbufk = nullptr,
-                          uint32_t* xbufv = nullptr);
 int ordered_sort_direct(uint64_t* keys, uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, int mode,
                         const uint8_t* skip, cudaStream_t s, uint64_t* xbufk = nullptr, uint32_t* xbufv = nullptr);
 size_t learned_workspace_bytes(int64_t n, double buffer_fraction);

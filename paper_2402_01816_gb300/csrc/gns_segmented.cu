@@ -46,16 +46,13 @@ struct SegChunk {
 // ---------------------------------------------------------------- plan
 // rows (each nseg + 1 long): row 0 = small-class tiles, row 1 = big-class tiles,
 // row 2 + p = merge chunks of level p.
-// skip (optional): segments flagged non-zero are left as they are (already in
-// order, e.g. all keys equal) and get no work.
 __global__ void seg_count_kernel(const int64_t* __restrict__ off, int64_t nseg, int L, int64_t small_max,
-                                 int64_t big_t, int64_t* rows, uint8_t* levels, const uint8_t* __restrict__ skip,
-                                 const int* ctl)
+                                 int64_t big_t, int64_t* rows, uint8_t* levels, const int* ctl)
 {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nseg || skip_all(ctl)) return;
     const int64_t stride = nseg + 1;
-    const int64_t len = (skip && skip[s]) ? 0 : off[s + 1] - off[s];
+    const int64_t len = off[s + 1] - off[s];
     const int64_t tiles = (len + big_t - 1) / big_t;
     int k = 0;
     while ((1ll << k) < tiles) ++k;
@@ -414,8 +411,6 @@ struct SegSchedule {
 };
 const SegSchedule kCandidates[] = {{0, 0, 4096}, {1024, 64, 4096}, {2048, 128, 4096}, {0, 0, 8192},
                                    {2048, 128, 8192}};
-// The learned path's buckets (tens of thousands of keys each): big tiles only.
-const SegSchedule kDirect = {0, 0, 8192};
 
 int max_levels(int64_t n)
 {
@@ -470,13 +465,12 @@ void seg_init_attributes()
 
 // Enqueues the whole segmented sort on s (keys/vals in place, ws laid out by lay).
 cudaError_t seg_enqueue(uint64_t* keys, uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, int mode,
-                        const SegSchedule& sch, char* ws, const SegLayout& lay, cudaStream_t s,
-                        const uint8_t* skip = nullptr, uint64_t* xbufk = nullptr, uint32_t* xbufv = nullptr)
+                        const SegSchedule& sch, char* ws, const SegLayout& lay, cudaStream_t s)
 {
     int* ctl = (int*)(ws + lay.ctl);
     int* call_err = ctl + 2;
-    uint64_t* bufk = xbufk ? xbufk : (uint64_t*)(ws + lay.bufk);
-    uint32_t* bufv = vals ? (xbufk ? xbufv : (uint32_t*)(ws + lay.bufv)) : nullptr;
+    uint64_t* bufk = (uint64_t*)(ws + lay.bufk);
+    uint32_t* bufv = vals ? (uint32_t*)(ws + lay.bufv) : nullptr;
     int64_t* rows = (int64_t*)(ws + lay.rows);
     uint8_t* levels = (uint8_t*)(ws + lay.levels);
     SegChunk* list = (SegChunk*)(ws + lay.list);
@@ -485,7 +479,7 @@ cudaError_t seg_enqueue(uint64_t* keys, uint32_t* vals, const int64_t* off, int6
     cudaError_t e = cudaMemsetAsync(ctl, 0, 256, s);
     if (e != cudaSuccess) return e;
     e = launch(K_SEG_PLAN, seg_count_kernel, dim3((unsigned)ceil_div(nseg, 256)), dim3(256), 0, s, off, nseg, lay.L,
-               sch.small_max, (int64_t)sch.big_t, rows, levels, skip, (const int*)ctl);
+               sch.small_max, (int64_t)sch.big_t, rows, levels, (const int*)ctl);
     if (e != cudaSuccess) return e;
     e = launch(K_SEG_PLAN, seg_scan_kernel, dim3((unsigned)(2 + lay.L)), dim3(1024), 0, s, rows, nseg,
                (const int*)ctl);
@@ -740,28 +734,12 @@ size_t segmented_workspace_bytes(int64_t n, int64_t nseg, bool ext_buf)
     return seg_layout(n, nseg, true, ext_buf).total;
 }
 
-// Segmented sort without tuning or graph capture (schedule 0), for callers that
-// build the segments themselves on the device (the learned-splitter sort).
-// xbufk / xbufv (optional): a caller-provided n-element ping-pong buffer.
-int segmented_sort_direct(uint64_t* keys, uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, int mode,
-                          const uint8_t* skip, cudaStream_t s, uint64_t* xbufk, uint32_t* xbufv)
-{
-    if (nseg == 0 || n <= 1) return GNS_OK;
-    seg_init_attributes();
-    const bool ext = xbufk != nullptr && (vals == nullptr || xbufv != nullptr);
-    const SegLayout lay = seg_layout(n, nseg, vals != nullptr, ext);
-    char* ws = (char*)ws_alloc(lay.total, s);
-    if (!ws) return GNS_ERR_OOM;
-    cudaError_t e = seg_enqueue(keys, vals, off, nseg, n, mode, kDirect, ws, lay, s, skip, ext ? xbufk : nullptr,
-                                ext ? xbufv : nullptr);
-    ws_free(ws, s);
-    return e == cudaSuccess ? GNS_OK : GNS_ERR_CUDA;
-}
-
-
-// Sort of ordered segments (see ord_count_kernel): the learned sort's buckets.
-// Same arguments and results as segmented_sort_direct; the segments must be
-// ordered, which the bucket check after the call verifies.
+// Sort of ordered segments (see ord_count_kernel): the learned sort's buckets,
+// built by the caller on the device.  off: nseg + 1 non-decreasing offsets
+// with off[nseg] = n; skip (optional): segments known to be all tied; xbufk /
+// xbufv (optional): a caller-provided n-element ping-pong buffer.  No tuning,
+// no graph capture.  The segments must be ordered, which the bucket check
+// after the call verifies.
 int ordered_sort_direct(uint64_t* keys, uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, int mode,
                         const uint8_t* skip, cudaStream_t s, uint64_t* xbufk, uint32_t* xbufv)
 {
