@@ -147,7 +147,7 @@ def test_learned_half_buffer_ram(L, n):
     assert nat.gns_workspace_bytes(n, 1.0, nat.WS_LEARNED) >= 16 * n
 
 
-@pytest.mark.parametrize("bf", [0.5, 0.75, 0.4, 0.25, 0.1, 1.0 / 64])
+@pytest.mark.parametrize("bf", [0.5, 0.75, 0.4, 0.3, 0.25, 0.125, 0.1, 1.0 / 32, 1.0 / 64])
 def test_frog_plan_invariants(L, bf):
     """The trees of the in-place tiers, built on the host by the library's own
     split (Frogsort1) and planner (Frogsort2): children split each node
